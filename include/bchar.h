@@ -1,0 +1,175 @@
+/*
+ * bchar.h -- C ABI of the GB300 B-char library (libbchar.so).
+ *
+ * One time step of the ball-approximated characteristics (B-char) method of
+ * Cheng & Droniou, "An efficient implementation of mass conserving
+ * characteristic-based schemes in 2D and 3D" (arXiv 1908.05834), for the pure
+ * advection problem  phi dc/dt + div(u c) = 0  with u.n = 0 on the boundary
+ * (Sec 1, eq. advection), on a tensor-product mesh of a box in 2D or 3D:
+ *
+ *   c^{n+1}_K = sum_M W_KM c^n_M,   W_KM = a_KM / |K|_phi   (Sec 2, eq. phys-inter-ELLAM)
+ *
+ * where a_KM approximates |M cap F_{-dt}(K)|_phi by balls (Sec 3, eq. ball_int),
+ * adjusted by N alternating scalings (Sec 3.2, eq. volAdj) and the
+ * mass-conservation minimisation (Sec 3.2, eq. opti_masscons).  Every stage
+ * runs in this library's own CUDA kernels on the stream given at creation.
+ *
+ * Conventions
+ *   - Every call returns a bchar_status by value; nothing throws across the ABI.
+ *     On error, bchar_last_error(mesh) gives a one-line description.
+ *   - Cells are numbered x fastest: k = i + n_x (j + n_y l).
+ *   - Face velocities of axis a are numbered the same way with n_a + 1 entries
+ *     along axis a (lowest-order Raviart-Thomas degrees of freedom: the
+ *     average normal velocity over each face, Sec 1.2 eq. hyp:un).
+ *   - Host pointers passed in are read before the call returns and not kept.
+ *   - c_in / c_out of bchar_step are DEVICE pointers owned by the caller.
+ *   - A mesh handle is used by one host thread at a time.  All device memory
+ *     it needs is owned by the handle and released by bchar_destroy.
+ */
+#ifndef BCHAR_H
+#define BCHAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bchar_mesh_s *bchar_mesh_t;
+
+typedef enum {
+    BCHAR_OK = 0,
+    BCHAR_ERR_INVALID_ARG = 1,   /* bad size, pointer, ordering or option   */
+    BCHAR_ERR_OUT_OF_MEMORY = 2, /* a device allocation failed              */
+    BCHAR_ERR_CUDA = 3,          /* a CUDA runtime call or kernel failed    */
+    BCHAR_ERR_BOUNDARY_FLUX = 4, /* u.n != 0 on the boundary (Sec 1)        */
+    BCHAR_ERR_DIVERGENCE = 5,    /* div u != 0 in a cell (Sec 2.2)          */
+    BCHAR_ERR_NONFINITE = 6,     /* NaN/Inf in an input                     */
+    BCHAR_ERR_NO_VELOCITY = 7,   /* bchar_step before bchar_set_velocity    */
+    BCHAR_ERR_CAPACITY = 8       /* a fixed internal limit was exceeded     */
+} bchar_status;
+
+/* Arithmetic of the tracking and intersection stages. */
+enum { BCHAR_FP64 = 0, BCHAR_FP32_SPLIT = 1 };
+/* Storage type of c. */
+enum { BCHAR_C_F64 = 0, BCHAR_C_F32 = 1 };
+
+typedef struct {
+    int balls_per_axis; /* nb: balls per axis on a cube cell (Sec 4: 4 balls in 2D, 8 in 3D -> 2) */
+    int n_scale;        /* N, alternating scalings before the minimisation (Sec 4: N = 10) */
+    int precision;      /* BCHAR_FP64: every stage in FP64.  BCHAR_FP32_SPLIT: tracking
+                           and ball intersections in FP32, all sums, the scalings, the
+                           minimisation and the update in FP64 */
+    int substeps;       /* RK4 substeps per step; 0 = smallest s with dt*vmax/s <= cfl*hmin */
+    double cfl;         /* 0.5 */
+    double drop_tol;    /* entries V_KM < drop_tol |K|_phi are dropped (1e-12) */
+    double penalty;     /* eps of the penalised minimisation (1e-7), see bchar_step */
+    double qp_tol;      /* stop when the L1 optimality residual <= qp_tol * sum |K|_phi (1e-14) */
+    int qp_max_iter;    /* cap on conjugate-gradient iterations per solve (200000) */
+    int qp_max_refine;  /* cap on refinement rounds (30) */
+    double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
+} bchar_options;
+
+typedef struct {
+    double mass_before;      /* sum_K |K|_phi c^n_K, FP64 (Sec 2.1) */
+    double mass_after;       /* sum_K |K|_phi c^{n+1}_K from the FP64 update, before any FP32 rounding */
+    double mass_after_stored;/* the same from the stored c_out */
+    double max_rel_row_res;  /* max_K |sum_M a_KM - |K|_phi| / |K|_phi  (eq. localmassconsMat) */
+    double max_rel_col_res;  /* max_M |sum_K a_KM - |M|_phi| / |M|_phi  (eq. globalmassconsMat) */
+    double scale_err;        /* max relative column error after the N scalings */
+    double kkt_rel;          /* final L1 optimality residual / sum |K|_phi of the minimisation */
+    int64_t nnz;             /* non-zeros of A */
+    int32_t substeps;        /* RK4 substeps used */
+    int32_t cg_iters;        /* conjugate-gradient iterations, all refinement rounds */
+    int32_t refines;         /* refinement rounds of the minimisation */
+    int32_t qp_converged;    /* 1 if kkt_rel <= qp_tol */
+    int32_t void_balls;      /* tracked balls that met no residing ball */
+    int32_t empty_cols;      /* residing cells no tracked ball reached (seeded) */
+    int32_t n_clipped;       /* entries whose 1 + x left [0, 2] */
+    int32_t kernel_launches; /* kernels launched by this call */
+} bchar_step_info;
+
+/* Fill *opt with the defaults listed above. */
+void bchar_default_options(bchar_options *opt);
+
+/* Create a mesh: the tensor-product partition of the box
+ * [coords[0][0], coords[0][n0]] x ... (Sec 1.2), porosity phi (Sec 1.2,
+ * eq. assump.global: piecewise constant, > 0) and its balls (Sec 3: n_K equal
+ * balls of radius min width / (2 nb), tightly packed, nb per axis on a cube).
+ *   dim       2 or 3
+ *   n_cells   dim counts, each >= 1 (and n_c = prod <= 2^31 - 1)
+ *   coords    dim HOST arrays of n_cells[a] + 1 strictly increasing doubles
+ *   phi       HOST array of n_c doubles, finite and > 0, x fastest
+ *   opt       NULL for the defaults
+ *   stream    cudaStream_t all work of this handle is ordered on (NULL = legacy default)
+ *   out       receives the handle (NULL on failure)
+ * Errors: INVALID_ARG, NONFINITE, OUT_OF_MEMORY, CUDA. */
+bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *const *coords,
+                               const double *phi, const bchar_options *opt, void *stream,
+                               bchar_mesh_t *out);
+
+/* Set the velocity u^{(n+1)} of the next step (Sec 1.2, eq. hyp:un): dim
+ * arrays of face-normal velocities (layout above, (n_a + 1) prod_{b != a} n_b
+ * doubles each), HOST pointers when on_device = 0, DEVICE pointers when 1
+ * (read on the handle's stream).  Checks that u.n = 0 on the boundary
+ * (Sec 1) and that every cell's net flux vanishes (div u = 0, Sec 2.2), both
+ * relative to the largest face velocity times div_tol.
+ * Errors: INVALID_ARG, NONFINITE, BOUNDARY_FLUX, DIVERGENCE, CUDA (the
+ * previous velocity is then discarded). */
+bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int on_device);
+
+/* One B-char time step of length dt > 0 (Algorithm 1 and eq. phys-inter-ELLAM):
+ *   1. every ball centre (and, if phi is not constant, the 2 dim points on
+ *      its axes at distance r) is tracked back along dF/dt = u/phi over dt by
+ *      classical RK4 (Sec 2 eq. charac, Sec 3 eq. rTrackedBall);
+ *   2. a^(0)_KM = V_{K,M} from the closed-form ball intersections
+ *      (Sec 3.1, eq. fracMaterial, eq. ball_int);
+ *   3. N alternating column/row scalings (Sec 3.2, eq. volAdj);
+ *   4. the minimisation of Sec 3.2 (eq. opti_masscons), read as: the
+ *      penalised minimum-norm adjustment x of min 1/2 x.x + 1/2 sum (s/(eps b))^2
+ *      (s the 2 n_c constraint residuals), then 1 + x clipped to the paper's
+ *      bounds [0, 2], then every column scaled to |M|_phi so that global mass
+ *      is conserved to rounding;
+ *   5. c_out = W c_in (eq. phys-inter-ELLAM), FP64 accumulation.
+ * c_in, c_out: DEVICE arrays of n_c values of type c_dtype, caller-owned, not
+ * aliased.  info: optional (NULL), written on return.  The call returns when
+ * the step has finished on the device.
+ * Errors: INVALID_ARG, NO_VELOCITY, OUT_OF_MEMORY, CAPACITY, CUDA. */
+bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out, int c_dtype,
+                        bchar_step_info *info);
+
+/* Release the handle and all its device memory (NULL is ignored). */
+void bchar_destroy(bchar_mesh_t m);
+
+/* Static text of a status code. */
+const char *bchar_status_string(bchar_status s);
+
+/* Detail of the last error on this handle ("" if none). */
+const char *bchar_last_error(bchar_mesh_t m);
+
+/* Number of cells n_c and of balls of the mesh. */
+int64_t bchar_cell_count(bchar_mesh_t m);
+int64_t bchar_ball_count(bchar_mesh_t m);
+
+/* Copy one matrix of the last step to HOST buffers in CSR form (rows =
+ * tracked cells K, columns = residing cells M, columns sorted in each row):
+ * which = 0: A^(0) (after seeding empty columns), 1: A^(N) after the
+ * scalings, 2: the final a_KM.  row_ptr gets n_c + 1 entries; cols / vals get
+ * nnz entries (cap = their capacity; *nnz_out receives nnz).  Errors:
+ * INVALID_ARG (no step yet, bad which), CAPACITY (cap < nnz), CUDA. */
+bchar_status bchar_export_matrix(bchar_mesh_t m, int which, int64_t *row_ptr, int32_t *cols,
+                                 double *vals, int64_t cap, int64_t *nnz_out);
+
+/* Copy the tracked balls of the last step to HOST buffers: pos[3 b + a] the
+ * tracked centre (absolute coordinates; a = 2 is 0 in 2D), rhat[b] the
+ * tracked radius, balls b of cell K numbered consecutively from
+ * ball_offset[K] (ball_offset: n_c + 1 entries).  cap = capacity in balls.
+ * Errors: INVALID_ARG, CAPACITY, CUDA. */
+bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int64_t *ball_offset,
+                                  int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCHAR_H */

@@ -1,0 +1,492 @@
+// The C ABI of libbchar (include/bchar.h): argument checks, device memory
+// owned by the handle, and the order of the kernels of one B-char step.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace bchar;
+
+namespace bchar {
+
+bool ensure(bchar_mesh_t m, Buf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return true;
+    if (b.p) {
+        cudaStreamSynchronize(m->stream);  // the old buffer may still be read by queued work
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    const size_t want = bytes < 256 ? 256 : bytes;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        char msg[128];
+        snprintf(msg, sizeof msg, "device allocation of %zu bytes failed", want);
+        m->err = msg;
+        return false;
+    }
+    b.bytes = want;
+    return true;
+}
+
+void release(Buf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+MeshView full_view(bchar_mesh_t m) {
+    MeshView v{};
+    v.dim = m->dim;
+    for (int a = 0; a < 3; ++a) {
+        v.n[a] = static_cast<int>(m->n[a]);
+        v.x[a] = ptr<double>(m->x[a]);
+        v.wd[a] = ptr<double>(m->wd[a]);
+        v.wf[a] = ptr<float>(m->wf[a]);
+    }
+    v.nc = m->nc;
+    v.phi = ptr<double>(m->phi);
+    v.phif = ptr<float>(m->phif);
+    v.volphi = ptr<double>(m->volphi);
+    v.rad = ptr<double>(m->rad);
+    v.radf = ptr<float>(m->radf);
+    v.rhophi = ptr<double>(m->rhophi);
+    v.rhophif = ptr<float>(m->rhophif);
+    v.cnt = ptr<int32_t>(m->cnt);
+    v.ball_off = ptr<int64_t>(m->ball_off);
+    v.ball_cell = ptr<int32_t>(m->ball_cell);
+    v.r_max = m->r_max;
+    return v;
+}
+
+VelView vel_view(bchar_mesh_t m) {
+    VelView v{};
+    for (int a = 0; a < m->dim; ++a) {
+        v.u[a] = ptr<double>(m->u[a]);
+        v.uf[a] = ptr<float>(m->uf[a]);
+    }
+    return v;
+}
+
+static double bits_to_double(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+}  // namespace bchar
+
+namespace {
+
+bchar_status fail(bchar_mesh_t m, bchar_status s, const char *msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+bchar_status cuda_check(bchar_mesh_t m) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        m->err = std::string("CUDA: ") + cudaGetErrorString(e);
+        return BCHAR_ERR_CUDA;
+    }
+    return BCHAR_OK;
+}
+
+DevInfo *host_info(bchar_mesh_t m) { return static_cast<DevInfo *>(m->info_host.p); }
+
+bchar_status read_info(bchar_mesh_t m) {
+    cudaMemcpyAsync(m->info_host.p, m->dinfo.p, sizeof(DevInfo), cudaMemcpyDeviceToHost, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return cuda_check(m);
+    return cuda_check(m);
+}
+
+bool options_valid(const bchar_options &o) {
+    return o.balls_per_axis >= 1 && o.balls_per_axis <= 8 && o.n_scale >= 0 && o.n_scale <= 100000 &&
+           (o.precision == BCHAR_FP64 || o.precision == BCHAR_FP32_SPLIT) && o.substeps >= 0 && o.cfl > 0.0 &&
+           o.drop_tol >= 0.0 && o.drop_tol < 1.0 && o.penalty > 0.0 && o.qp_tol > 0.0 && o.qp_max_iter >= 0 &&
+           o.qp_max_refine >= 0 && o.div_tol > 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bchar_default_options(bchar_options *o) {
+    if (!o) return;
+    o->balls_per_axis = 2;
+    o->n_scale = 10;
+    o->precision = BCHAR_FP64;
+    o->substeps = 0;
+    o->cfl = 0.5;
+    o->drop_tol = 1e-12;
+    o->penalty = 1e-7;
+    o->qp_tol = 1e-14;
+    o->qp_max_iter = 200000;
+    o->qp_max_refine = 30;
+    o->div_tol = 1e-9;
+}
+
+const char *bchar_status_string(bchar_status s) {
+    switch (s) {
+    case BCHAR_OK: return "ok";
+    case BCHAR_ERR_INVALID_ARG: return "invalid argument";
+    case BCHAR_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case BCHAR_ERR_CUDA: return "CUDA error";
+    case BCHAR_ERR_BOUNDARY_FLUX: return "velocity has a normal component on the boundary";
+    case BCHAR_ERR_DIVERGENCE: return "velocity is not divergence free";
+    case BCHAR_ERR_NONFINITE: return "non-finite input";
+    case BCHAR_ERR_NO_VELOCITY: return "no velocity set";
+    case BCHAR_ERR_CAPACITY: return "internal capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *bchar_last_error(bchar_mesh_t m) { return m ? m->err.c_str() : ""; }
+
+int64_t bchar_cell_count(bchar_mesh_t m) { return m ? m->nc : 0; }
+int64_t bchar_ball_count(bchar_mesh_t m) { return m ? m->nballs : 0; }
+
+void bchar_destroy(bchar_mesh_t m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    Buf *all[] = {&m->phi, &m->phif, &m->volphi, &m->rad, &m->radf, &m->rhophi, &m->rhophif, &m->cnt,
+                  &m->ball_off, &m->ball_cell, &m->t_cell, &m->t_xi, &m->t_rhat, &m->slab_col, &m->slab_val,
+                  &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
+                  &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->a2,
+                  &m->a2c, &m->diag, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
+                  &m->cg_q, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
+    for (Buf *b : all) release(*b);
+    for (int a = 0; a < 3; ++a) {
+        release(m->x[a]);
+        release(m->wd[a]);
+        release(m->wf[a]);
+        release(m->u[a]);
+        release(m->uf[a]);
+    }
+    if (m->info_host.p) cudaFreeHost(m->info_host.p);
+    delete m;
+}
+
+bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *const *coords, const double *phi,
+                               const bchar_options *opt, void *stream, bchar_mesh_t *out) {
+    if (!out) return BCHAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || !n_cells || !coords || !phi) return BCHAR_ERR_INVALID_ARG;
+    bchar_options o;
+    bchar_default_options(&o);
+    if (opt) o = *opt;
+    if (!options_valid(o)) return BCHAR_ERR_INVALID_ARG;
+    int64_t n[3] = {1, 1, 1}, nc = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (n_cells[a] < 1 || n_cells[a] > (1 << 30) || !coords[a]) return BCHAR_ERR_INVALID_ARG;
+        n[a] = n_cells[a];
+        nc *= n[a];
+        if (nc > 0x7fffffffLL) return BCHAR_ERR_INVALID_ARG;
+    }
+    double hmin = INFINITY, sum_vp = 0.0;
+    for (int a = 0; a < dim; ++a)
+        for (int64_t i = 0; i <= n[a]; ++i) {
+            if (!isfinite(coords[a][i])) return BCHAR_ERR_NONFINITE;
+            if (i > 0) {
+                double w = coords[a][i] - coords[a][i - 1];
+                if (!(w > 0.0)) return BCHAR_ERR_INVALID_ARG;
+                hmin = w < hmin ? w : hmin;
+            }
+        }
+    bool phi_const = true;
+    for (int64_t k = 0; k < nc; ++k) {
+        if (!isfinite(phi[k])) return BCHAR_ERR_NONFINITE;
+        if (!(phi[k] > 0.0)) return BCHAR_ERR_INVALID_ARG;
+        if (phi[k] != phi[0]) phi_const = false;
+    }
+    for (int64_t k = 0; k < nc; ++k) {
+        int64_t c[3] = {k % n[0], (k / n[0]) % n[1], k / (n[0] * n[1])};
+        double v = phi[k];
+        for (int a = 0; a < dim; ++a) v *= coords[a][c[a] + 1] - coords[a][c[a]];
+        sum_vp += v;
+    }
+
+    bchar_mesh_t m = new bchar_mesh_s();
+    m->dim = dim;
+    m->nb = o.balls_per_axis;
+    for (int a = 0; a < 3; ++a) m->n[a] = n[a];
+    m->nc = nc;
+    m->opt = o;
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->phi_const = phi_const;
+    m->hmin = hmin;
+    m->sum_volphi = sum_vp;
+
+    bool ok = true;
+    for (int a = 0; a < dim; ++a) {
+        ok = ok && ensure(m, m->x[a], sizeof(double) * (n[a] + 1)) && ensure(m, m->wd[a], sizeof(double) * n[a]) &&
+             ensure(m, m->wf[a], sizeof(float) * n[a]);
+    }
+    for (int a = dim; a < 3; ++a) {  // unit extent along the missing axis
+        ok = ok && ensure(m, m->x[a], sizeof(double) * 2) && ensure(m, m->wd[a], sizeof(double)) &&
+             ensure(m, m->wf[a], sizeof(float));
+    }
+    ok = ok && ensure(m, m->phi, sizeof(double) * nc) && ensure(m, m->phif, sizeof(float) * nc) &&
+         ensure(m, m->volphi, sizeof(double) * nc) && ensure(m, m->rad, sizeof(double) * nc) &&
+         ensure(m, m->radf, sizeof(float) * nc) && ensure(m, m->rhophi, sizeof(double) * nc) &&
+         ensure(m, m->rhophif, sizeof(float) * nc) && ensure(m, m->cnt, sizeof(int32_t) * nc) &&
+         ensure(m, m->ball_off, sizeof(int64_t) * (nc + 1)) && ensure(m, m->colcnt, sizeof(int32_t) * nc) &&
+         ensure(m, m->colfill, sizeof(int32_t) * nc) && ensure(m, m->row_len, sizeof(int32_t) * nc) &&
+         ensure(m, m->row_ptr, sizeof(int64_t) * (nc + 1)) && ensure(m, m->col_ptr, sizeof(int64_t) * (nc + 1)) &&
+         ensure(m, m->R, sizeof(double) * nc) && ensure(m, m->C, sizeof(double) * nc) &&
+         ensure(m, m->seeds, sizeof(unsigned long long) * kMaxSeeds) &&
+         ensure(m, m->diag, sizeof(double) * 2 * nc) && ensure(m, m->rhs, sizeof(double) * 2 * nc) &&
+         ensure(m, m->qy, sizeof(double) * 2 * nc) && ensure(m, m->F, sizeof(double) * 2 * nc) &&
+         ensure(m, m->cg_d, sizeof(double) * 2 * nc) && ensure(m, m->cg_r, sizeof(double) * 2 * nc) &&
+         ensure(m, m->cg_z, sizeof(double) * 2 * nc) && ensure(m, m->cg_p, sizeof(double) * 2 * nc) &&
+         ensure(m, m->cg_q, sizeof(double) * 2 * nc) && ensure(m, m->partials, sizeof(double) * 4 * 152 * 64) &&
+         ensure(m, m->dinfo, sizeof(DevInfo)) && ensure(m, m->cg, sizeof(CgState));
+    if (ok && cudaMallocHost(&m->info_host.p, sizeof(DevInfo) + sizeof(CgState)) != cudaSuccess) {
+        cudaGetLastError();
+        m->info_host.p = nullptr;
+        ok = false;
+    }
+    if (!ok) {
+        bchar_destroy(m);
+        return BCHAR_ERR_OUT_OF_MEMORY;
+    }
+    for (int a = 0; a < dim; ++a)
+        cudaMemcpyAsync(m->x[a].p, coords[a], sizeof(double) * (n[a] + 1), cudaMemcpyHostToDevice, m->stream);
+    const double unit[2] = {0.0, 1.0};
+    for (int a = dim; a < 3; ++a) cudaMemcpyAsync(m->x[a].p, unit, sizeof unit, cudaMemcpyHostToDevice, m->stream);
+    cudaMemcpyAsync(m->phi.p, phi, sizeof(double) * nc, cudaMemcpyHostToDevice, m->stream);
+    cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
+    launch_mesh_setup(m);
+    for (int a = dim; a < 3; ++a) {  // widths of the missing axis (launch_mesh_setup covers dim axes)
+        const double one = 1.0;
+        const float onef = 1.0f;
+        cudaMemcpyAsync(m->wd[a].p, &one, sizeof one, cudaMemcpyHostToDevice, m->stream);
+        cudaMemcpyAsync(m->wf[a].p, &onef, sizeof onef, cudaMemcpyHostToDevice, m->stream);
+    }
+    int64_t nballs = 0;
+    cudaMemcpyAsync(&nballs, ptr<int64_t>(m->ball_off) + nc, sizeof nballs, cudaMemcpyDeviceToHost, m->stream);
+    bchar_status st = read_info(m);
+    if (st != BCHAR_OK) {
+        bchar_destroy(m);
+        return st;
+    }
+    if (host_info(m)->err & kErrBallsPerCell) {
+        bchar_destroy(m);
+        return BCHAR_ERR_CAPACITY;
+    }
+    m->nballs = nballs;
+    m->r_max = bits_to_double(host_info(m)->umax_bits);
+    const size_t rb = o.precision == BCHAR_FP32_SPLIT ? sizeof(float) : sizeof(double);
+    ok = ensure(m, m->ball_cell, sizeof(int32_t) * nballs) && ensure(m, m->t_cell, sizeof(int32_t) * nballs) &&
+         ensure(m, m->t_xi, rb * 3 * nballs) && ensure(m, m->t_rhat, rb * nballs);
+    m->row_cap = dim == 2 ? 24 : 64;
+    ok = ok && ensure(m, m->slab_col, sizeof(int32_t) * nc * m->row_cap) &&
+         ensure(m, m->slab_val, sizeof(double) * nc * m->row_cap);
+    if (!ok) {
+        bchar_destroy(m);
+        return BCHAR_ERR_OUT_OF_MEMORY;
+    }
+    launch_ball_cells(m);
+    st = read_info(m);
+    if (st != BCHAR_OK) {
+        bchar_destroy(m);
+        return st;
+    }
+    *out = m;
+    return BCHAR_OK;
+}
+
+bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int on_device) {
+    if (!m) return BCHAR_ERR_INVALID_ARG;
+    m->err.clear();
+    if (!face_u) return fail(m, BCHAR_ERR_INVALID_ARG, "face_u is NULL");
+    m->has_velocity = false;
+    for (int a = 0; a < m->dim; ++a) {
+        if (!face_u[a]) return fail(m, BCHAR_ERR_INVALID_ARG, "a face velocity array is NULL");
+        int64_t nf = 1;
+        for (int b = 0; b < m->dim; ++b) nf *= m->n[b] + (b == a ? 1 : 0);
+        m->nface[a] = nf;
+        if (!ensure(m, m->u[a], sizeof(double) * nf) || !ensure(m, m->uf[a], sizeof(float) * nf))
+            return BCHAR_ERR_OUT_OF_MEMORY;
+        cudaMemcpyAsync(m->u[a].p, face_u[a], sizeof(double) * nf,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
+    }
+    cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
+    launch_velocity_check(m);
+    bchar_status st = read_info(m);
+    if (st != BCHAR_OK) return st;
+    const DevInfo *h = host_info(m);
+    if (h->nonfinite) return fail(m, BCHAR_ERR_NONFINITE, "non-finite face velocity");
+    const double umax = bits_to_double(h->umax_bits);
+    const double bflux = bits_to_double(h->bflux_bits);
+    const double div = bits_to_double(h->div_bits);
+    if (bflux > m->opt.div_tol * umax) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "max |u.n| on the boundary %.3e exceeds div_tol * max|u| = %.3e", bflux,
+                 m->opt.div_tol * umax);
+        return fail(m, BCHAR_ERR_BOUNDARY_FLUX, msg);
+    }
+    if (div > m->opt.div_tol) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "a cell's net flux is %.3e of its total face flux (div_tol %.1e)", div,
+                 m->opt.div_tol);
+        return fail(m, BCHAR_ERR_DIVERGENCE, msg);
+    }
+    m->vmax = bits_to_double(h->vmax_bits);
+    m->has_velocity = true;
+    return BCHAR_OK;
+}
+
+bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out, int c_dtype,
+                        bchar_step_info *info) {
+    if (!m) return BCHAR_ERR_INVALID_ARG;
+    m->err.clear();
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(m, BCHAR_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!c_in || !c_out || c_in == c_out) return fail(m, BCHAR_ERR_INVALID_ARG, "c_in / c_out NULL or aliased");
+    if (c_dtype != BCHAR_C_F64 && c_dtype != BCHAR_C_F32) return fail(m, BCHAR_ERR_INVALID_ARG, "bad c_dtype");
+    if (!m->has_velocity) return fail(m, BCHAR_ERR_NO_VELOCITY, "bchar_set_velocity first");
+    m->launches = 0;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, m->stream);
+
+    // substeps: the smallest s with dt * vmax / s <= cfl * hmin
+    int substeps = m->opt.substeps;
+    if (substeps <= 0) {
+        double s = ceil(dt * m->vmax / (m->opt.cfl * m->hmin));
+        if (!(s <= 1e6)) return fail(m, BCHAR_ERR_INVALID_ARG, "dt needs more than 1e6 RK4 substeps");
+        substeps = s < 1.0 ? 1 : static_cast<int>(s);
+    }
+    cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
+    launch_track(m, dt, substeps);
+
+    // initial weights, row by row, into the slab; grow the slab if a row is wider
+    DevInfo *h = host_info(m);
+    bchar_status st;
+    for (int attempt = 0;; ++attempt) {
+        launch_assemble(m);
+        launch_column_counts(m);
+        launch_seed_columns(m, dt, substeps);
+        if ((st = read_info(m)) != BCHAR_OK) return st;
+        if ((h->err & kErrRowCapacity) && attempt < 2) {
+            int cap = (h->need_row_cap + 7) / 8 * 8;
+            if (!ensure(m, m->slab_col, sizeof(int32_t) * m->nc * cap) ||
+                !ensure(m, m->slab_val, sizeof(double) * m->nc * cap))
+                return BCHAR_ERR_OUT_OF_MEMORY;
+            m->row_cap = cap;
+            cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
+            continue;
+        }
+        break;
+    }
+    if (h->err) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "capacity error bits 0x%x during assembly", h->err);
+        return fail(m, BCHAR_ERR_CAPACITY, msg);
+    }
+    const int void_balls = h->void_balls;
+    const int nseeds = h->n_seeds;
+    if (nseeds > 0) {
+        launch_insert_seeds(m, nseeds);
+        if ((st = read_info(m)) != BCHAR_OK) return st;
+        if (h->err) return fail(m, BCHAR_ERR_CAPACITY, "a seeded row overflowed its slab row");
+    }
+
+    // CSR and its column view
+    scan_i32_to_i64(m, ptr<int32_t>(m->row_len), ptr<int64_t>(m->row_ptr), m->nc);
+    int64_t nnz = 0;
+    cudaMemcpyAsync(&nnz, ptr<int64_t>(m->row_ptr) + m->nc, sizeof nnz, cudaMemcpyDeviceToHost, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return cuda_check(m);
+    if (nnz >= 0x7fffffffLL) return fail(m, BCHAR_ERR_CAPACITY, "more than 2^31 - 1 non-zeros");
+    m->nnz = nnz;
+    const size_t z = nnz > 0 ? static_cast<size_t>(nnz) : 1;
+    if (!ensure(m, m->col, sizeof(int32_t) * z) || !ensure(m, m->a0, sizeof(double) * z) ||
+        !ensure(m, m->aN, sizeof(double) * z) || !ensure(m, m->afin, sizeof(double) * z) ||
+        !ensure(m, m->wgt, sizeof(double) * z) || !ensure(m, m->qx, sizeof(double) * z) ||
+        !ensure(m, m->a2, sizeof(double) * z) || !ensure(m, m->a2c, sizeof(double) * z) ||
+        !ensure(m, m->csc_row, sizeof(int32_t) * z) || !ensure(m, m->csc_src, sizeof(int32_t) * z))
+        return BCHAR_ERR_OUT_OF_MEMORY;
+    launch_compact(m);
+    launch_transpose(m);
+
+    // N alternating scalings, the minimisation, bounds and column fix, update
+    launch_scaling(m);
+    int cg_iters = 0, refines = 0;
+    launch_minimise(m, &cg_iters, &refines);
+    launch_finalise(m);
+    launch_update(m, c_in, c_out, c_dtype);
+    cudaEventRecord(ev1, m->stream);
+    if ((st = read_info(m)) != BCHAR_OK) return st;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    m->have_step = true;
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->mass_before = h->mass_before;
+        info->mass_after = h->mass_after;
+        info->mass_after_stored = h->mass_after_stored;
+        info->max_rel_row_res = h->max_rel_row_res;
+        info->max_rel_col_res = h->max_rel_col_res;
+        info->scale_err = h->scale_err;
+        info->kkt_rel = h->kkt_l1 / m->sum_volphi;
+        info->nnz = nnz;
+        info->substeps = substeps;
+        info->cg_iters = cg_iters;
+        info->refines = refines;
+        info->qp_converged = info->kkt_rel <= m->opt.qp_tol;
+        info->void_balls = void_balls;
+        info->empty_cols = nseeds;
+        info->n_clipped = h->n_clipped;
+        info->kernel_launches = m->launches;
+    }
+    (void)ms;
+    return BCHAR_OK;
+}
+
+bchar_status bchar_export_matrix(bchar_mesh_t m, int which, int64_t *row_ptr, int32_t *cols, double *vals,
+                                 int64_t cap, int64_t *nnz_out) {
+    if (!m) return BCHAR_ERR_INVALID_ARG;
+    if (!m->have_step || which < 0 || which > 2 || !row_ptr || !cols || !vals)
+        return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet or bad arguments");
+    if (nnz_out) *nnz_out = m->nnz;
+    if (cap < m->nnz) return fail(m, BCHAR_ERR_CAPACITY, "cap < nnz");
+    const Buf &src = which == 0 ? m->a0 : (which == 1 ? m->aN : m->afin);
+    cudaMemcpyAsync(row_ptr, m->row_ptr.p, sizeof(int64_t) * (m->nc + 1), cudaMemcpyDeviceToHost, m->stream);
+    cudaMemcpyAsync(cols, m->col.p, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost, m->stream);
+    cudaMemcpyAsync(vals, src.p, sizeof(double) * m->nnz, cudaMemcpyDeviceToHost, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return cuda_check(m);
+    return cuda_check(m);
+}
+
+bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int64_t *ball_offset, int64_t cap) {
+    if (!m) return BCHAR_ERR_INVALID_ARG;
+    if (!m->have_step || !pos || !rhat || !ball_offset) return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet");
+    if (cap < m->nballs) return fail(m, BCHAR_ERR_CAPACITY, "cap < number of balls");
+    Buf dpos, drh;
+    if (!ensure(m, dpos, sizeof(double) * 3 * m->nballs) || !ensure(m, drh, sizeof(double) * m->nballs)) {
+        release(dpos);
+        release(drh);
+        return BCHAR_ERR_OUT_OF_MEMORY;
+    }
+    launch_export_tracked(m, ptr<double>(dpos), ptr<double>(drh));
+    cudaMemcpyAsync(pos, dpos.p, sizeof(double) * 3 * m->nballs, cudaMemcpyDeviceToHost, m->stream);
+    cudaMemcpyAsync(rhat, drh.p, sizeof(double) * m->nballs, cudaMemcpyDeviceToHost, m->stream);
+    cudaMemcpyAsync(ball_offset, m->ball_off.p, sizeof(int64_t) * (m->nc + 1), cudaMemcpyDeviceToHost, m->stream);
+    cudaStreamSynchronize(m->stream);
+    release(dpos);
+    release(drh);
+    return cuda_check(m);
+}
+
+}  // extern "C"
+
+namespace bchar {
+double total_volphi(bchar_mesh_t m) { return m->sum_volphi; }
+}  // namespace bchar

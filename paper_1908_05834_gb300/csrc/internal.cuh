@@ -1,0 +1,169 @@
+// Internal declarations of libbchar: the state behind a bchar_mesh_t, the
+// plain-old-data views handed to kernels, and the launch helpers shared by
+// the kernel files.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bchar.h"
+
+namespace bchar {
+
+constexpr int kThreads = 256;     // threads per block of the element-wise kernels
+constexpr int kScanChunk = 4096;  // elements per block of the device-wide scan
+constexpr int kMaxSeeds = 4096;   // empty columns handled per step
+constexpr int kMaxBallsPerCell = 32;
+
+// Device error word bits (BCHAR_ERR_CAPACITY causes).
+enum : int {
+    kErrBallsPerCell = 1,   // a cell has more than kMaxBallsPerCell balls
+    kErrRowCapacity = 2,    // a row has more entries than the slab row capacity
+    kErrWindow = 4,         // a candidate window is larger than the window limit
+    kErrSeeds = 8,          // more than kMaxSeeds empty columns
+    kErrSeedCapacity = 16,  // a seeded row overflowed the slab row capacity
+};
+
+// Read-only mesh data passed by value to kernels.
+struct MeshView {
+    int dim;
+    int n[3];               // cells per axis (n[2] = 1 in 2D)
+    int64_t nc;
+    const double *x[3];     // node coordinates per axis
+    const double *wd[3];    // cell widths per axis, FP64
+    const float *wf[3];     // cell widths per axis, FP32
+    const double *phi;      // porosity per cell
+    const float *phif;
+    const double *volphi;   // |K|_phi
+    const double *rad;      // ball radius r_K
+    const float *radf;
+    const double *rhophi;   // rho_K phi_K = |K|_phi / (n_K |B_K|)
+    const float *rhophif;
+    const int32_t *cnt;     // balls per axis, packed n_x | n_y << 8 | n_z << 16
+    const int64_t *ball_off;  // first ball of each cell, n_c + 1
+    const int32_t *ball_cell; // cell of each ball
+    double r_max;
+};
+
+// Face velocities of the current step.
+struct VelView {
+    const double *u[3];
+    const float *uf[3];
+};
+
+// Scalars produced on the device during a step, copied to the host once.
+struct DevInfo {
+    double mass_before, mass_after, mass_after_stored;
+    double max_rel_row_res, max_rel_col_res, scale_err;
+    double kkt_l1, f_l1;
+    unsigned long long vmax_bits;   // max |u|/phi as the bits of a non-negative double
+    unsigned long long umax_bits;   // max |u| over all faces
+    unsigned long long bflux_bits;  // max |u.n| over boundary faces
+    unsigned long long div_bits;    // max relative net flux of a cell
+    int nonfinite;
+    int err;            // capacity error bits
+    int need_row_cap;   // largest row length seen
+    int void_balls;
+    int n_seeds;
+    int n_clipped;
+    long long nnz;
+};
+
+// Conjugate-gradient scalars.
+struct CgState {
+    double rz, rz_new, pq, alpha, beta, res_l1, target;
+    int converged;
+    int iters;
+};
+
+// A growable device buffer.
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace bchar
+
+struct bchar_mesh_s {
+    int dim = 0;
+    int nb = 2;
+    int64_t n[3] = {1, 1, 1};
+    int64_t nc = 0;
+    int64_t nballs = 0;
+    int max_balls = 0;
+    bool phi_const = false;
+    double hmin = 0.0;
+    double r_max = 0.0;
+    double sum_volphi = 0.0;
+    bchar_options opt{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // persistent mesh data
+    bchar::Buf x[3], wd[3], wf[3], phi, phif, volphi, rad, radf, rhophi, rhophif, cnt, ball_off, ball_cell;
+    // velocity
+    bchar::Buf u[3], uf[3];
+    int64_t nface[3] = {0, 0, 0};
+    bool has_velocity = false;
+    double vmax = 0.0;
+
+    // per-step buffers
+    bchar::Buf t_cell, t_xi, t_rhat;                 // tracked balls
+    bchar::Buf slab_col, slab_val, row_len;          // per-row assembly slab
+    int row_cap = 0;
+    bchar::Buf colcnt, colfill, seeds, seed_row_cnt; // columns, empty-column seeds
+    bchar::Buf row_ptr, col_ptr;                     // CSR / CSC pointers
+    bchar::Buf col, a0, aN, afin, wgt;               // CSR entries
+    bchar::Buf csc_row, csc_src;                     // CSC: row and CSR index of each entry
+    bchar::Buf R, C;                                 // scaling factors
+    bchar::Buf a2, a2c, diag, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
+    bchar::Buf scan_tmp, partials, dinfo, cg;        // scratch
+    bchar::Buf info_host;                            // pinned DevInfo
+    int64_t nnz = 0;
+    bool have_step = false;
+    int launches = 0;
+};
+
+namespace bchar {
+
+// ---- host helpers (capi.cu) ------------------------------------------------
+bool ensure(bchar_mesh_t m, Buf &b, size_t bytes);
+void release(Buf &b);
+double total_volphi(bchar_mesh_t m);  // sum of |K|_phi over the mesh
+
+template <class T> inline T *ptr(Buf &b) { return static_cast<T *>(b.p); }
+
+inline int blocks_for(int64_t n, int threads = kThreads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;  // grid-stride beyond this
+    return static_cast<int>(b);
+}
+
+// ---- kernels launched from capi.cu ------------------------------------------
+// mesh.cu
+void launch_mesh_setup(bchar_mesh_t m);
+void launch_ball_cells(bchar_mesh_t m);
+void launch_velocity_check(bchar_mesh_t m);
+// track.cu
+void launch_track(bchar_mesh_t m, double dt, int substeps);
+void launch_seed_columns(bchar_mesh_t m, double dt, int substeps);
+// assemble.cu
+void launch_assemble(bchar_mesh_t m);
+void launch_column_counts(bchar_mesh_t m);
+void launch_insert_seeds(bchar_mesh_t m, int nseeds);
+void launch_compact(bchar_mesh_t m);
+void launch_export_tracked(bchar_mesh_t m, double *pos, double *rhat);
+MeshView full_view(bchar_mesh_t m);
+VelView vel_view(bchar_mesh_t m);
+// sparse.cu
+void scan_i32_to_i64(bchar_mesh_t m, const int32_t *in, int64_t *out, int64_t n);  // out has n + 1 entries
+void launch_transpose(bchar_mesh_t m);
+void launch_scaling(bchar_mesh_t m);
+void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines);
+void launch_finalise(bchar_mesh_t m);
+void launch_update(bchar_mesh_t m, const void *c_in, void *c_out, int c_dtype);
+
+}  // namespace bchar

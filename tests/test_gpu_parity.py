@@ -1,0 +1,257 @@
+"""GPU path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Sizes are chosen so the oracle finishes in seconds while the GPU kernels
+still see several blocks/warps and ragged tails (cell counts that are not
+multiples of 32), plus sampled rows and invariants at the full workload sizes.
+
+Tolerances (from the arithmetic):
+  * FP64 mode: tracked points and A^(0), A^(N) differ from the oracle only by
+    rounding order (~1e-15 relative); 1e-10 is used.  Final weights and c
+    also depend on how far each side solved the penalised minimisation: the
+    bar is 1e-5 of the row maximum for W and 1e-5 relative L1 for c.
+  * FP32-split mode: tracking and intersections in FP32 (6e-8 relative per
+    operation, ~1e-6 of a ball radius after the RK4 substeps); a stage point
+    that lands within rounding of a face can take the neighbouring cell's
+    field, so a few rows may differ by more.  Bar: c within 1e-5 relative L1,
+    99.9 % of rows of A^(0) within 1e-4 of the row maximum; the measured
+    maximum is reported.
+  * Mass: |M^{n+1} - M^n| <= 1e-12 M^n on the GPU in both modes.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_1908_05834_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1908_05834_gb300 import build
+    build.build()
+    from paper_1908_05834_gb300 import bchar
+    return bchar
+
+
+def _case(name):
+    if name == "uniform2d":
+        wl = inputs.workload("vortex2d_32", n=37)
+    elif name == "stretched2d":
+        wl = inputs.workload("vortex2d_1024", n=45)
+    elif name == "porous3d":
+        wl = inputs.workload("deform3d_128", n=11)
+    elif name == "stretched3d":
+        wl = inputs.workload("deform3d_256", n=9)
+    else:
+        raise KeyError(name)
+    return wl
+
+
+def _gpu_step(bc, wl, faces, c, precision=0, **opt):
+    import torch
+    o = bc.default_options(precision=precision, **opt)
+    mesh = bc.Mesh(wl.coords, wl.phi, o)
+    mesh.set_velocity(faces)
+    dt = torch.float32 if np.asarray(c).dtype == np.float32 else torch.float64
+    c_in = torch.tensor(np.asarray(c), dtype=dt, device="cuda")
+    c_out = torch.empty_like(c_in)
+    info = mesh.step(wl.dt, c_in, c_out)
+    return mesh, info, c_out.cpu().numpy()
+
+
+def _csr(mesh, which):
+    rp, cols, vals = mesh.export_matrix(which)
+    return sp.csr_matrix((vals, cols, rp), shape=(mesh.nc, mesh.nc))
+
+
+def _row_rel_err(A, B):
+    """max over rows of max |A - B| / max |B| in the row (absent entries = 0)."""
+    D = (A - B).tocsr()
+    Bm = abs(B).max(axis=1).toarray().ravel()
+    Dm = abs(D).max(axis=1).toarray().ravel()
+    return Dm / np.where(Bm > 0, Bm, 1.0)
+
+
+CASES = ["uniform2d", "stretched2d", "porous3d", "stretched3d"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_tracked_balls_match_oracle_fp64(bc, name):
+    wl = _case(name)
+    faces = wl.faces(3)
+    mesh, info, _ = _gpu_step(bc, wl, faces, wl.c0.astype(np.float64))
+    pos, rh, off = mesh.export_tracked()
+    om = oracle.Mesh(wl.coords, wl.phi)
+    s = oracle.substep_count(om, faces, wl.dt)
+    assert info["substeps"] == s
+    ooff, ocen, orh = oracle.track_balls(om, faces, wl.dt, s, np.arange(om.nc))
+    assert np.array_equal(off, ooff)
+    h = min(float(np.min(np.diff(c))) for c in wl.coords)
+    assert np.max(np.abs(pos - ocen)) <= 1e-10 * h
+    assert np.max(np.abs(rh - orh)) <= 1e-10 * h
+    mesh.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_matrices_match_oracle_fp64(bc, name):
+    wl = _case(name)
+    faces = wl.faces(3)
+    c = wl.c0.astype(np.float64)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c)
+    ref = oracle.step(oracle.Mesh(wl.coords, wl.phi), faces, wl.dt, c)
+    A0, AN, A = _csr(mesh, 0), _csr(mesh, 1), _csr(mesh, 2)
+    assert info["void_balls"] == ref["void_balls"] and info["empty_cols"] == ref["empty_cols"]
+    assert np.max(_row_rel_err(A0, ref["A0"])) <= 1e-10
+    assert np.max(_row_rel_err(AN, ref["AN"])) <= 1e-9
+    # final weights: the bar is 1e-5 of the row maximum
+    vp = oracle.Mesh(wl.coords, wl.phi).volphi()
+    W = sp.diags(1.0 / vp) @ A
+    assert np.max(_row_rel_err(W.tocsr(), ref["W"])) <= 1e-5
+    err = np.abs(c_gpu - ref["c"]).sum() / np.abs(ref["c"]).sum()
+    assert err <= 1e-5
+    assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    assert info["max_rel_col_res"] <= 1e-13
+    mesh.close()
+
+
+def test_vortex32_full_run_fp64(bc):
+    """The 32x32 steady vortex, all 20 steps, GPU and oracle side by side."""
+    import torch
+    wl = inputs.workload("vortex2d_32")
+    om = oracle.Mesh(wl.coords, wl.phi)
+    mesh = bc.Mesh(wl.coords, wl.phi, bc.default_options())
+    c_ref = wl.c0.astype(np.float64)
+    c_gpu = torch.tensor(c_ref, device="cuda")
+    out = torch.empty_like(c_gpu)
+    m0 = oracle.total_mass(om, c_ref)
+    for st in range(wl.steps):
+        faces = wl.faces(st)
+        mesh.set_velocity(faces)
+        info = mesh.step(wl.dt, c_gpu, out)
+        c_gpu, out = out, c_gpu
+        c_ref = oracle.step(om, faces, wl.dt, c_ref)["c"]
+        g = c_gpu.cpu().numpy()
+        assert np.abs(g - c_ref).sum() / np.abs(c_ref).sum() <= 1e-5, st
+        assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * m0
+    mesh.close()
+
+
+@pytest.mark.parametrize("name", ["stretched2d", "porous3d"])
+def test_fp32_split_error_budget(bc, name):
+    wl = _case(name)
+    faces = wl.faces(3)
+    c = wl.c0.astype(np.float64)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c, precision=bc.FP32_SPLIT)
+    ref = oracle.step(oracle.Mesh(wl.coords, wl.phi), faces, wl.dt, c)
+    e0 = _row_rel_err(_csr(mesh, 0), ref["A0"])
+    frac_ok = np.mean(e0 <= 1e-4)
+    err_c = np.abs(c_gpu - ref["c"]).sum() / np.abs(ref["c"]).sum()
+    print(f"\n{name} FP32 split: A0 max row err {e0.max():.2e}, rows within 1e-4: {frac_ok:.4%}, c L1 {err_c:.2e}")
+    assert frac_ok >= 0.999
+    assert err_c <= 1e-5
+    assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    mesh.close()
+
+
+@pytest.mark.parametrize("name,precision", [("vortex2d_1024", 1), ("deform3d_128", 1)])
+def test_full_size_sampled_rows(bc, name, precision):
+    """Full workload size, one step in the benchmarked configuration: sampled
+    rows of A^(0) recomputed one by one by the oracle, plus invariants."""
+    wl = inputs.workload(name)
+    faces = wl.faces(0)
+    c = wl.c0.astype(np.float64)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c, precision=precision, qp_max_iter=4000)
+    om = oracle.Mesh(wl.coords, wl.phi)
+    rng = np.random.Generator(np.random.PCG64(99))
+    rows = np.sort(rng.choice(om.nc, size=48, replace=False))
+    s = oracle.substep_count(om, faces, wl.dt)
+    assert info["substeps"] == s
+    off, cen, rh = oracle.track_balls(om, faces, wl.dt, s, rows)
+    rl, cols, vals, _ = oracle.assemble_rows(om, faces, off, cen, rh, rows)
+    A0 = _csr(mesh, 0)
+    start = 0
+    bad = 0
+    for r, n in zip(rows, rl):
+        want = dict(zip(cols[start:start + n], vals[start:start + n]))
+        start += n
+        got = A0.getrow(int(r))
+        gotd = dict(zip(got.indices, got.data))
+        keys = set(want) | set(gotd)
+        mx = max(want.values())
+        e = max(abs(gotd.get(k, 0.0) - want.get(k, 0.0)) for k in keys) / mx
+        bad += e > 1e-4
+    assert bad <= 1  # a stage point within FP32 rounding of a face may flip one row
+    vp = om.volphi()
+    rowsum = np.asarray(A0.sum(axis=1)).ravel()
+    assert np.max(np.abs(rowsum - vp) / vp) <= 1e-5  # eq. ball_int row identity, FP32 fractions
+    assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    assert info["max_rel_col_res"] <= 1e-13
+    assert np.all(c_gpu >= 0)
+    mesh.close()
+
+
+def test_step_is_bitwise_reproducible(bc):
+    wl = _case("stretched2d")
+    faces = wl.faces(1)
+    c = wl.c0.astype(np.float64)
+    m1, _, c1 = _gpu_step(bc, wl, faces, c, precision=bc.FP32_SPLIT)
+    m2, _, c2 = _gpu_step(bc, wl, faces, c, precision=bc.FP32_SPLIT)
+    assert np.array_equal(c1, c2)
+    assert np.array_equal(m1.export_matrix(2)[2], m2.export_matrix(2)[2])
+    m1.close()
+    m2.close()
+
+
+def test_zero_velocity_is_identity_on_gpu(bc):
+    wl = _case("porous3d")
+    faces = [np.zeros_like(f) for f in wl.faces(0)]
+    c = np.random.Generator(np.random.PCG64(4)).uniform(size=wl.nc)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c)
+    assert info["nnz"] == wl.nc
+    assert np.allclose(c_gpu, c, rtol=1e-13, atol=0)
+    mesh.close()
+
+
+def test_error_statuses(bc):
+    import torch
+    wl = _case("uniform2d")
+    faces = wl.faces(0)
+    mesh = bc.Mesh(wl.coords, wl.phi)
+    c = torch.zeros(wl.nc, dtype=torch.float64, device="cuda")
+    out = torch.zeros_like(c)
+    with pytest.raises(bc.BcharError) as e:
+        mesh.step(wl.dt, c, out)
+    assert e.value.name == "NO_VELOCITY"
+    bad = [f.copy() for f in faces]
+    bad[0][:, 0] = 0.3  # flux through the left wall
+    with pytest.raises(bc.BcharError) as e:
+        mesh.set_velocity(bad)
+    assert e.value.name == "BOUNDARY_FLUX"
+    bad = [f.copy() for f in faces]
+    bad[0][5, 7] += 0.1  # a source in two cells
+    with pytest.raises(bc.BcharError) as e:
+        mesh.set_velocity(bad)
+    assert e.value.name == "DIVERGENCE"
+    bad = [f.copy() for f in faces]
+    bad[1][3, 3] = np.nan
+    with pytest.raises(bc.BcharError) as e:
+        mesh.set_velocity(bad)
+    assert e.value.name == "NONFINITE"
+    mesh.set_velocity(faces)
+    with pytest.raises(bc.BcharError) as e:
+        mesh.step(-1.0, c, out)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(bc.BcharError) as e:
+        mesh.step(wl.dt, c, c)
+    assert e.value.name == "INVALID_ARG"
+    mesh.close()
+    with pytest.raises(bc.BcharError) as e:
+        bc.Mesh([wl.coords[0][::-1], wl.coords[1]], wl.phi)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(bc.BcharError) as e:
+        bc.Mesh(wl.coords, -wl.phi)
+    assert e.value.name == "INVALID_ARG"

@@ -68,6 +68,8 @@ typedef struct {
     int qp_max_iter;    /* cap on conjugate-gradient iterations per solve (200000) */
     int qp_max_refine;  /* cap on refinement rounds (30) */
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
+    int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
+                           1 = aggregation multigrid (default), 0 = Jacobi */
 } bchar_options;
 
 typedef struct {
@@ -87,6 +89,8 @@ typedef struct {
     int32_t empty_cols;      /* residing cells no tracked ball reached (seeded) */
     int32_t n_clipped;       /* entries whose 1 + x left [0, 2] */
     int32_t kernel_launches; /* kernels launched by this call */
+    int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
+    int32_t amg_coarsest;    /* unknowns on its coarsest level */
 } bchar_step_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -167,6 +171,22 @@ bchar_status bchar_export_matrix(bchar_mesh_t m, int which, int64_t *row_ptr, in
  * Errors: INVALID_ARG, CAPACITY, CUDA. */
 bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int64_t *ball_offset,
                                   int64_t cap);
+
+/* Stages that bchar_time_stage can replay. */
+enum {
+    BCHAR_STAGE_CG_MATVEC = 0, /* one product with A-hat A-hat^T + W (the minimisation's inner loop) */
+    BCHAR_STAGE_UPDATE = 1,    /* c^{n+1} = W c^n and the mass sums */
+    BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
+    BCHAR_STAGE_TRACK = 3      /* RK4 tracking of all balls */
+};
+
+/* Measurement aid: replay the kernel of one stage `reps` times on the data of
+ * the last step, on the handle's stream, and return the mean duration of one
+ * launch in milliseconds (CUDA events around the replays).  The replays do
+ * not change the result of the last step (exports stay valid) except that
+ * BCHAR_STAGE_TRACK overwrites the tracked balls with the same values.
+ * Errors: INVALID_ARG (no step yet, bad stage, reps < 1), CUDA. */
+bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
     _fields_ = [("balls_per_axis", ctypes.c_int), ("n_scale", ctypes.c_int), ("precision", ctypes.c_int),
                 ("substeps", ctypes.c_int), ("cfl", ctypes.c_double), ("drop_tol", ctypes.c_double),
                 ("penalty", ctypes.c_double), ("qp_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int),
-                ("qp_max_refine", ctypes.c_int), ("div_tol", ctypes.c_double)]
+                ("qp_max_refine", ctypes.c_int), ("div_tol", ctypes.c_double), ("qp_precond", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -37,7 +37,8 @@ class StepInfo(ctypes.Structure):
                 ("max_rel_col_res", ctypes.c_double), ("scale_err", ctypes.c_double), ("kkt_rel", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("substeps", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
                 ("refines", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
-                ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+                ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -81,6 +82,11 @@ lib.bchar_export_matrix.restype = ctypes.c_int
 lib.bchar_export_tracked.argtypes = [_H, _P, _P, _P, _I64]
 lib.bchar_export_tracked.restype = ctypes.c_int
 
+lib.bchar_time_stage.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+lib.bchar_time_stage.restype = ctypes.c_int
+
+STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK = 0, 1, 2, 3
+
 bchar_default_options = lib.bchar_default_options
 bchar_create_mesh = lib.bchar_create_mesh
 bchar_set_velocity = lib.bchar_set_velocity
@@ -90,6 +96,7 @@ bchar_status_string = lib.bchar_status_string
 bchar_last_error = lib.bchar_last_error
 bchar_export_matrix = lib.bchar_export_matrix
 bchar_export_tracked = lib.bchar_export_tracked
+bchar_time_stage = lib.bchar_time_stage
 
 
 def default_options(**kw) -> Options:
@@ -187,6 +194,12 @@ class Mesh:
         self._check(lib.bchar_export_tracked(self.handle, pos.ctypes.data, rh.ctypes.data, off.ctypes.data,
                                              self.nballs), "export_tracked")
         return pos, rh, off
+
+    def time_stage(self, stage: int, reps: int = 20) -> float:
+        """Mean milliseconds of one launch of a stage's kernel, replayed on the last step's data."""
+        ms = ctypes.c_float(0.0)
+        self._check(lib.bchar_time_stage(self.handle, stage, reps, ctypes.byref(ms)), "time_stage")
+        return float(ms.value)
 
     def close(self):
         if getattr(self, "handle", None):

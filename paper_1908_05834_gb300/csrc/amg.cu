@@ -1,0 +1,436 @@
+// Aggregation multigrid preconditioner for the minimisation's linear system.
+//
+// The system (A-hat A-hat^T + W) y = F of the penalised minimisation is, after
+// flipping the sign of the column unknowns (S = diag(1 rows, -1 columns)), the
+// M-matrix L = [[D_r, -W], [-W^T, D_c]] + diag(w): a weighted graph Laplacian
+// of the bipartite row/column graph (edge weights a_ij^2) plus a small
+// positive shift.  Its conditioning is poor on two counts: mesh-scale smooth
+// modes, and weak links (near-tangent ball overlaps give a_ij that are orders
+// of magnitude below the row's main entries).  Aggregating along the strongest
+// links handles both:
+//   - each level pairs every node with its heaviest neighbour when the choice
+//     is mutual (kHandshakes rounds, each among the nodes still unpaired);
+//     unpaired nodes stay single, and coarsening stops when a level would
+//     keep more than kStall of its nodes;
+//   - the coarse operator is the Galerkin product P^T L P for the piecewise-
+//     constant P of the aggregates (coarse edge = sum of fine edges between
+//     two aggregates).  Its diagonal is formed as the coarse node's excess
+//     (the sum of its members' shifts) plus the sum of its coarse edge
+//     weights, not as member diagonals minus internal edges: the shift is
+//     ~1e-14 of the edge weights and the subtraction would cancel it away;
+//   - a symmetric V-cycle (one damped-Jacobi sweep before and after the
+//     coarse correction, Jacobi sweeps on the coarsest level) is applied as
+//     the preconditioner of the conjugate gradients.
+// Every sum runs in a fixed order, so the hierarchy and its application are
+// deterministic.
+#include <math.h>
+
+#include "amg.cuh"
+#include "device.cuh"
+
+namespace bchar {
+
+#define GRID_STRIDE(i, n)                                                                    \
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < (n); \
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
+constexpr int kCoarseCap = 384;       // neighbours a coarse node may collect before merging
+constexpr int64_t kCoarsest = 1024;   // stop coarsening below this many nodes
+constexpr int64_t kOneBlock = 4096;   // coarsest levels up to this size are swept by one block
+constexpr int kMaxLevels = 40;
+constexpr int kHandshakes = 4;        // matching rounds per level
+constexpr double kStall = 0.9;        // stop coarsening when a level keeps this fraction of nodes
+constexpr double kOmega = 0.6;        // Jacobi damping
+constexpr int kCoarsestSweeps = 40;   // one-block coarsest solve
+constexpr int kLargeCoarsestSweeps = 20;
+
+// ---------------------------------------------------------------- level 0
+
+// Row node l < nc: its entries come from row l of A (columns nc + j);
+// column node nc + j: from column j (rows i).  Values -a_ij^2.
+__global__ void k_level0_ptr(int64_t nc, int64_t nnz, const int64_t *row_ptr, const int64_t *col_ptr,
+                             int64_t *ptr0) {
+    GRID_STRIDE(l, 2 * nc + 1) ptr0[l] = l <= nc ? row_ptr[l] : nnz + col_ptr[l - nc];
+}
+
+__global__ void k_level0_fill(int64_t nc, const int64_t *row_ptr, const int32_t *col, const int64_t *col_ptr,
+                              const int32_t *csc_row, const double *a2, const double *a2c, const int64_t *ptr0,
+                              int32_t *col0, double *val0) {
+    GRID_STRIDE(l, 2 * nc) {
+        int64_t dst = ptr0[l];
+        if (l < nc) {
+            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e, ++dst) {
+                col0[dst] = static_cast<int32_t>(nc + col[e]);
+                val0[dst] = -a2[e];
+            }
+        } else {
+            const int64_t j = l - nc;
+            for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p, ++dst) {
+                col0[dst] = csc_row[p];
+                val0[dst] = -a2c[p];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- matching
+
+// Heaviest neighbour (most negative off-diagonal), ties to the smaller index;
+// with only_free, among neighbours that are still unpaired.
+__global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
+                           const int32_t *partner, int only_free, int32_t *best) {
+    GRID_STRIDE(i, n) {
+        int32_t b = -1;
+        double bw = 0.0;
+        if (!only_free || partner[i] < 0) {
+            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+                const int32_t j = col[e];
+                if (j == i) continue;
+                if (only_free && partner[j] >= 0) continue;
+                const double w = -val[e];
+                if (w > bw || (w == bw && w > 0.0 && j < b)) {
+                    bw = w;
+                    b = j;
+                }
+            }
+        }
+        best[i] = b;
+    }
+}
+
+__global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
+    GRID_STRIDE(i, n) {
+        if (partner[i] >= 0) continue;
+        const int32_t b = best[i];
+        if (b >= 0 && best[b] == i) partner[i] = b;
+    }
+}
+
+__global__ void k_leaders(int64_t n, const int32_t *partner, int32_t *is_leader) {
+    GRID_STRIDE(i, n) {
+        const int32_t p = partner[i];
+        is_leader[i] = (p < 0 || i < p) ? 1 : 0;
+    }
+}
+
+// agg[i] = coarse index of i's aggregate; members[2 I + {0,1}] its nodes.
+__global__ void k_aggregates(int64_t n, const int32_t *partner, const int64_t *leader_pos, int32_t *agg,
+                             int32_t *members) {
+    GRID_STRIDE(i, n) {
+        const int32_t p = partner[i];
+        const int64_t lead = (p < 0 || i < p) ? i : p;
+        const int64_t I = leader_pos[lead];
+        agg[i] = static_cast<int32_t>(I);
+        if (lead == i) {
+            members[2 * I] = static_cast<int32_t>(i);
+            members[2 * I + 1] = p;  // -1 for a single node
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Galerkin coarse operator
+
+// Collect, sort and merge the coarse neighbours of coarse node I (internal
+// edges drop out of the Laplacian).  Returns the number of distinct
+// neighbours (or -1 on overflow); *eI receives the coarse excess.
+__device__ int coarse_row(int64_t I, const int32_t *members, const int64_t *ptr, const int32_t *col,
+                          const double *val, const double *exc, const int32_t *agg, int32_t *cbuf, double *vbuf,
+                          double *eI) {
+    int cnt = 0;
+    double e_sum = 0.0;
+    for (int k = 0; k < 2; ++k) {
+        const int32_t m = members[2 * I + k];
+        if (m < 0) continue;
+        e_sum += exc[m];
+        for (int64_t e = ptr[m]; e < ptr[m + 1]; ++e) {
+            const int32_t J = agg[col[e]];
+            if (J == I) continue;
+            // insertion into the sorted buffer, merging equal columns
+            int pos = cnt;
+            while (pos > 0 && cbuf[pos - 1] > J) --pos;
+            if (pos > 0 && cbuf[pos - 1] == J) {
+                vbuf[pos - 1] += val[e];
+                continue;
+            }
+            if (cnt == kCoarseCap) return -1;
+            for (int q = cnt; q > pos; --q) {
+                cbuf[q] = cbuf[q - 1];
+                vbuf[q] = vbuf[q - 1];
+            }
+            cbuf[pos] = J;
+            vbuf[pos] = val[e];
+            ++cnt;
+        }
+    }
+    *eI = e_sum;
+    return cnt;
+}
+
+__global__ void k_coarse_count(int64_t nco, const int32_t *members, const int64_t *ptr, const int32_t *col,
+                               const double *val, const double *exc, const int32_t *agg, int32_t *rowcnt,
+                               int *overflow) {
+    int32_t cbuf[kCoarseCap];
+    double vbuf[kCoarseCap];
+    GRID_STRIDE(I, nco) {
+        double e;
+        const int c = coarse_row(I, members, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        if (c < 0) {
+            atomicOr(overflow, 1);
+            rowcnt[I] = 0;
+        } else {
+            rowcnt[I] = c;
+        }
+    }
+}
+
+__global__ void k_coarse_fill(int64_t nco, const int32_t *members, const int64_t *ptr, const int32_t *col,
+                              const double *val, const double *exc, const int32_t *agg, const int64_t *cptr,
+                              int32_t *ccol, double *cval, double *cdiag, double *cexc) {
+    int32_t cbuf[kCoarseCap];
+    double vbuf[kCoarseCap];
+    GRID_STRIDE(I, nco) {
+        double e;
+        const int c = coarse_row(I, members, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        const int64_t dst = cptr[I];
+        double d = e;
+        for (int k = 0; k < c; ++k) {
+            ccol[dst + k] = cbuf[k];
+            cval[dst + k] = vbuf[k];
+            d -= vbuf[k];
+        }
+        cdiag[I] = d;
+        cexc[I] = e;
+    }
+}
+
+// ---------------------------------------------------------------- V-cycle kernels
+
+__global__ void k_flip_copy(int64_t nc, const double *in, double *out, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(l, 2 * nc) out[l] = l < nc ? in[l] : -in[l];
+}
+
+// x = omega b / diag
+__global__ void k_jacobi0(int64_t n, const double *diag, const double *b, double *x, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) x[i] = kOmega * b[i] / diag[i];
+}
+
+// r = b - L x
+__global__ void k_residual(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
+                           const double *x, const double *b, double *r, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) {
+        double s = diag[i] * x[i];
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
+        r[i] = b[i] - s;
+    }
+}
+
+// x_out = x + omega (b - L x) / diag
+__global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
+                         const double *x, const double *b, double *x_out, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) {
+        double s = diag[i] * x[i];
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
+        x_out[i] = x[i] + kOmega * (b[i] - s) / diag[i];
+    }
+}
+
+__global__ void k_restrict(int64_t nco, const int32_t *members, const double *r, double *bc, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(I, nco) {
+        const int32_t m1 = members[2 * I + 1];
+        bc[I] = r[members[2 * I]] + (m1 >= 0 ? r[m1] : 0.0);
+    }
+}
+
+__global__ void k_prolong(int64_t n, const int32_t *agg, const double *xc, double *x, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) x[i] += xc[agg[i]];
+}
+
+// Coarsest level: kCoarsestSweeps damped-Jacobi sweeps from zero, all in one
+// block (the level is small), double-buffered in global memory.
+__global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
+                           const double *b, double *x, double *x2, const CgState *st) {
+    if (st && st->converged) return;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = kOmega * b[i] / diag[i];
+    __syncthreads();
+    for (int k = 0; k < kCoarsestSweeps; ++k) {
+        const double *xi = (k & 1) ? x2 : x;
+        double *xo = (k & 1) ? x : x2;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            double s = diag[i] * xi[i];
+            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * xi[col[e]];
+            xo[i] = xi[i] + kOmega * (b[i] - s) / diag[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+void amg_release(Amg &amg) {
+    for (AmgLevel &L : amg.levels) {
+        Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.members, &L.x, &L.x2, &L.b, &L.r};
+        for (Buf *b : all) release(*b);
+    }
+    amg.levels.clear();
+    release(amg.tmp);
+}
+
+static bool level_vectors(bchar_mesh_t m, AmgLevel &L) {
+    // x holds n + 1 entries: it doubles as the int64 scan output while coarsening
+    return ensure(m, L.x, sizeof(double) * (L.n + 1)) && ensure(m, L.x2, sizeof(double) * L.n) &&
+           ensure(m, L.b, sizeof(double) * L.n) && ensure(m, L.r, sizeof(double) * L.n);
+}
+
+bool amg_build(bchar_mesh_t m, Amg &amg) {
+    cudaStream_t s = m->stream;
+    const int64_t nc = m->nc, nnz = m->nnz;
+    if (amg.levels.empty()) amg.levels.resize(1);
+    amg.nlev = 1;
+    AmgLevel &L0 = amg.levels[0];
+    L0.n = 2 * nc;
+    L0.nnz = 2 * nnz;
+    if (!ensure(m, L0.ptr, sizeof(int64_t) * (L0.n + 1)) || !ensure(m, L0.col, sizeof(int32_t) * L0.nnz) ||
+        !ensure(m, L0.val, sizeof(double) * L0.nnz) || !level_vectors(m, L0))
+        return false;
+    L0.diag_ext = ptr<double>(m->diag);
+    L0.exc_ext = ptr<double>(m->qexc);
+    k_level0_ptr<<<blocks_for(L0.n + 1), kThreads, 0, s>>>(nc, nnz, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
+                                                           ptr<int64_t>(L0.ptr));
+    k_level0_fill<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                                                        ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
+                                                        ptr<double>(m->a2), ptr<double>(m->a2c),
+                                                        ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
+                                                        ptr<double>(L0.val));
+    m->launches += 2;
+    if (!ensure(m, amg.tmp, sizeof(int32_t) * 3 * L0.n + 64)) return false;
+    while (amg.nlev < kMaxLevels) {
+        AmgLevel &F = amg.levels[amg.nlev - 1];
+        if (F.n <= kCoarsest) break;
+        const double *fexc = F.exc_ext ? F.exc_ext : ptr<double>(F.exc);
+        if (!ensure(m, amg.tmp, sizeof(int32_t) * 3 * F.n + 64) || !ensure(m, F.agg, sizeof(int32_t) * F.n))
+            return false;
+        int32_t *best = ptr<int32_t>(amg.tmp);
+        int32_t *partner = best + F.n;
+        int32_t *lead = partner + F.n;
+        int *overflow = reinterpret_cast<int *>(lead + F.n);
+        const int bl = blocks_for(F.n);
+        cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * F.n, s);
+        cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        for (int round = 0; round < kHandshakes; ++round) {
+            k_heaviest<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
+                                               partner, round > 0, best);
+            k_handshake<<<bl, kThreads, 0, s>>>(F.n, best, partner);
+            m->launches += 2;
+        }
+        k_leaders<<<bl, kThreads, 0, s>>>(F.n, partner, lead);
+        // leader positions: scan of the leader flags (int32 -> int64), reuse the
+        // per-level x buffer as int64 scratch (n + 1 entries fit in x and x2)
+        int64_t *pos = reinterpret_cast<int64_t *>(ptr<double>(F.x));
+        scan_i32_to_i64(m, lead, pos, F.n);
+        int64_t nco = 0;
+        cudaMemcpyAsync(&nco, pos + F.n, sizeof nco, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        if (nco >= F.n * kStall || nco < 1) break;  // matching stalled: this is the coarsest level
+        if (static_cast<int>(amg.levels.size()) <= amg.nlev) amg.levels.resize(amg.nlev + 1);
+        AmgLevel &Fr = amg.levels[amg.nlev - 1];  // re-fetch after resize
+        AmgLevel &C = amg.levels[amg.nlev];
+        C.n = nco;
+        C.diag_ext = nullptr;
+        C.exc_ext = nullptr;
+        if (!ensure(m, C.members, sizeof(int32_t) * 2 * nco) || !ensure(m, C.ptr, sizeof(int64_t) * (nco + 1)) ||
+            !ensure(m, C.diag, sizeof(double) * nco) || !ensure(m, C.exc, sizeof(double) * nco) ||
+            !level_vectors(m, C))
+            return false;
+        k_aggregates<<<bl, kThreads, 0, s>>>(Fr.n, partner, pos, ptr<int32_t>(Fr.agg), ptr<int32_t>(C.members));
+        int32_t *rowcnt = lead;  // the leader flags are no longer needed
+        k_coarse_count<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int32_t>(C.members), ptr<int64_t>(Fr.ptr),
+                                                            ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
+                                                            ptr<int32_t>(Fr.agg), rowcnt, overflow);
+        scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
+        int64_t cnnz = 0;
+        int ovf = 0;
+        cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + nco, sizeof cnnz, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&ovf, overflow, sizeof ovf, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        m->launches += 3;
+        if (ovf) break;  // a coarse row would be too wide: stop at the finer level
+        C.nnz = cnnz;
+        if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
+            !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
+            return false;
+        k_coarse_fill<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int32_t>(C.members), ptr<int64_t>(Fr.ptr),
+                                                           ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
+                                                           ptr<int32_t>(Fr.agg), ptr<int64_t>(C.ptr),
+                                                           ptr<int32_t>(C.col), ptr<double>(C.val),
+                                                           ptr<double>(C.diag), ptr<double>(C.exc));
+        ++m->launches;
+        ++amg.nlev;
+    }
+    return true;
+}
+
+static const double *level_diag(const AmgLevel &L) {
+    return L.diag_ext ? L.diag_ext : static_cast<const double *>(L.diag.p);
+}
+
+// z = S V(S res): one V-cycle of the sign-flipped operator on the residual.
+void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st) {
+    cudaStream_t s = m->stream;
+    const int64_t nc = m->nc;
+    AmgLevel &L0 = amg.levels[0];
+    k_flip_copy<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, ptr<double>(L0.b), st);
+    ++m->launches;
+    // down: pre-smooth from zero, residual, restrict
+    for (int l = 0; l < amg.nlev - 1; ++l) {
+        AmgLevel &L = amg.levels[l];
+        AmgLevel &C = amg.levels[l + 1];
+        const int bl = blocks_for(L.n);
+        k_jacobi0<<<bl, kThreads, 0, s>>>(L.n, level_diag(L), ptr<double>(L.b), ptr<double>(L.x), st);
+        k_residual<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
+                                           level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.r), st);
+        k_restrict<<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int32_t>(C.members), ptr<double>(L.r),
+                                                        ptr<double>(C.b), st);
+        m->launches += 3;
+    }
+    // coarsest: Jacobi sweeps from zero (an even number, so the result is in x);
+    // one block when the level is small, otherwise one launch per sweep
+    {
+        AmgLevel &L = amg.levels[amg.nlev - 1];
+        if (L.n <= kOneBlock) {
+            k_coarsest<<<1, 1024, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
+                                          level_diag(L), ptr<double>(L.b), ptr<double>(L.x), ptr<double>(L.x2), st);
+            ++m->launches;
+        } else {
+            const int bl = blocks_for(L.n);
+            k_jacobi0<<<bl, kThreads, 0, s>>>(L.n, level_diag(L), ptr<double>(L.b), ptr<double>(L.x), st);
+            for (int k = 0; k < kLargeCoarsestSweeps; ++k) {
+                k_jacobi<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
+                                                 level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.x2),
+                                                 st);
+                std::swap(L.x, L.x2);
+            }
+            m->launches += 1 + kLargeCoarsestSweeps;
+        }
+    }
+    // up: prolong, post-smooth
+    for (int l = amg.nlev - 2; l >= 0; --l) {
+        AmgLevel &L = amg.levels[l];
+        AmgLevel &C = amg.levels[l + 1];
+        const int bl = blocks_for(L.n);
+        k_prolong<<<bl, kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), ptr<double>(C.x), ptr<double>(L.x), st);
+        k_jacobi<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
+                                         level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.x2), st);
+        std::swap(L.x, L.x2);
+        m->launches += 2;
+    }
+    k_flip_copy<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<double>(L0.x), z, st);
+    ++m->launches;
+}
+
+}  // namespace bchar

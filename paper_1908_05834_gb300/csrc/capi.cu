@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include "amg.cuh"
 #include "internal.cuh"
 
 using namespace bchar;
@@ -108,7 +109,7 @@ bool options_valid(const bchar_options &o) {
     return o.balls_per_axis >= 1 && o.balls_per_axis <= 8 && o.n_scale >= 0 && o.n_scale <= 100000 &&
            (o.precision == BCHAR_FP64 || o.precision == BCHAR_FP32_SPLIT) && o.substeps >= 0 && o.cfl > 0.0 &&
            o.drop_tol >= 0.0 && o.drop_tol < 1.0 && o.penalty > 0.0 && o.qp_tol > 0.0 && o.qp_max_iter >= 0 &&
-           o.qp_max_refine >= 0 && o.div_tol > 0.0;
+           o.qp_max_refine >= 0 && o.div_tol > 0.0 && (o.qp_precond == 0 || o.qp_precond == 1);
 }
 
 }  // namespace
@@ -128,6 +129,7 @@ void bchar_default_options(bchar_options *o) {
     o->qp_max_iter = 200000;
     o->qp_max_refine = 30;
     o->div_tol = 1e-9;
+    o->qp_precond = 1;
 }
 
 const char *bchar_status_string(bchar_status s) {
@@ -157,7 +159,7 @@ void bchar_destroy(bchar_mesh_t m) {
                   &m->ball_off, &m->ball_cell, &m->t_cell, &m->t_xi, &m->t_rhat, &m->slab_col, &m->slab_val,
                   &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
                   &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->a2,
-                  &m->a2c, &m->diag, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
+                  &m->a2c, &m->diag, &m->qexc, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
                   &m->cg_q, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
     for (Buf *b : all) release(*b);
     for (int a = 0; a < 3; ++a) {
@@ -168,6 +170,7 @@ void bchar_destroy(bchar_mesh_t m) {
         release(m->uf[a]);
     }
     if (m->info_host.p) cudaFreeHost(m->info_host.p);
+    amg_release(m->amg);
     delete m;
 }
 
@@ -240,6 +243,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
          ensure(m, m->R, sizeof(double) * nc) && ensure(m, m->C, sizeof(double) * nc) &&
          ensure(m, m->seeds, sizeof(unsigned long long) * kMaxSeeds) &&
          ensure(m, m->diag, sizeof(double) * 2 * nc) && ensure(m, m->rhs, sizeof(double) * 2 * nc) &&
+         ensure(m, m->qexc, sizeof(double) * 2 * nc) &&
          ensure(m, m->qy, sizeof(double) * 2 * nc) && ensure(m, m->F, sizeof(double) * 2 * nc) &&
          ensure(m, m->cg_d, sizeof(double) * 2 * nc) && ensure(m, m->cg_r, sizeof(double) * 2 * nc) &&
          ensure(m, m->cg_z, sizeof(double) * 2 * nc) && ensure(m, m->cg_p, sizeof(double) * 2 * nc) &&
@@ -427,6 +431,8 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     m->have_step = true;
+    m->substeps = substeps;
+    m->dt = dt;
     if (info) {
         memset(info, 0, sizeof *info);
         info->mass_before = h->mass_before;
@@ -445,6 +451,8 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->empty_cols = nseeds;
         info->n_clipped = h->n_clipped;
         info->kernel_launches = m->launches;
+        info->amg_levels = m->amg_levels;
+        info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);
     }
     (void)ms;
     return BCHAR_OK;
@@ -482,6 +490,48 @@ bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int
     cudaStreamSynchronize(m->stream);
     release(dpos);
     release(drh);
+    return cuda_check(m);
+}
+
+bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms) {
+    if (!m) return BCHAR_ERR_INVALID_ARG;
+    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 3)
+        return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet or bad arguments");
+    Buf st, cin, cout;
+    if (!ensure(m, st, sizeof(CgState)) || !ensure(m, cin, sizeof(double) * m->nc) ||
+        !ensure(m, cout, sizeof(double) * m->nc)) {
+        release(st);
+        release(cin);
+        release(cout);
+        return BCHAR_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemsetAsync(st.p, 0, sizeof(CgState), m->stream);
+    cudaMemsetAsync(cin.p, 0, sizeof(double) * m->nc, m->stream);
+    // the final weights are kept in wgt; the slab of the assembly is scratch
+    auto once = [&]() {
+        switch (stage) {
+        case BCHAR_STAGE_CG_MATVEC: launch_cg_matvec_once(m, ptr<CgState>(st)); break;
+        case BCHAR_STAGE_UPDATE: launch_update(m, cin.p, cout.p, BCHAR_C_F64); break;
+        case BCHAR_STAGE_ASSEMBLE: launch_assemble(m); break;
+        default: launch_track(m, m->dt, m->substeps); break;
+        }
+    };
+    once();  // warm-up
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, m->stream);
+    for (int r = 0; r < reps; ++r) once();
+    cudaEventRecord(e1, m->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *mean_ms = ms / reps;
+    release(st);
+    release(cin);
+    release(cout);
     return cuda_check(m);
 }
 

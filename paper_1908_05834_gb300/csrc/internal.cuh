@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "bchar.h"
 
@@ -84,6 +85,22 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// One level of the multigrid hierarchy: a symmetric CSR operator (off-diagonal
+// entries only) with its diagonal, the map to the next coarser level and the
+// members of each of its aggregates, plus work vectors.
+struct AmgLevel {
+    int64_t n = 0, nnz = 0;
+    Buf ptr, col, val, diag, exc, agg, members, x, x2, b, r;
+    const double *diag_ext = nullptr;  // level 0 shares the minimisation's diagonal
+    const double *exc_ext = nullptr;   // and its excess (the penalty shift)
+};
+
+struct Amg {
+    std::vector<AmgLevel> levels;
+    int nlev = 0;
+    Buf tmp;
+};
+
 }  // namespace bchar
 
 struct bchar_mesh_s {
@@ -118,10 +135,15 @@ struct bchar_mesh_s {
     bchar::Buf col, a0, aN, afin, wgt;               // CSR entries
     bchar::Buf csc_row, csc_src;                     // CSC: row and CSR index of each entry
     bchar::Buf R, C;                                 // scaling factors
-    bchar::Buf a2, a2c, diag, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
+    bchar::Buf a2, a2c, diag, qexc, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
     bchar::Buf scan_tmp, partials, dinfo, cg;        // scratch
     bchar::Buf info_host;                            // pinned DevInfo
+    bchar::Amg amg;                                  // preconditioner of the minimisation
     int64_t nnz = 0;
+    int substeps = 1;
+    double dt = 0.0;
+    int amg_levels = 0;
+    int64_t amg_coarsest = 0;
     bool have_step = false;
     int launches = 0;
 };
@@ -165,5 +187,7 @@ void launch_scaling(bchar_mesh_t m);
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines);
 void launch_finalise(bchar_mesh_t m);
 void launch_update(bchar_mesh_t m, const void *c_in, void *c_out, int c_dtype);
+void launch_cg_matvec_once(bchar_mesh_t m, CgState *st);  // q = J p with the current p, for timing
+int last_substeps(bchar_mesh_t m);
 
 }  // namespace bchar

@@ -18,6 +18,7 @@
 // bitwise reproducible.
 #include <math.h>
 
+#include "amg.cuh"
 #include "device.cuh"
 
 namespace bchar {
@@ -240,7 +241,7 @@ void launch_scaling(bchar_mesh_t m) {
 // w_l = (eps b_l)^2.
 __global__ void k_qp_setup(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
                            const double *aN, const double *volphi, double eps, double *a2, double *diag,
-                           double *rhs) {
+                           double *exc, double *rhs) {
     GRID_STRIDE(l, 2 * nc) {
         double d = 0.0, s = 0.0;
         if (l < nc) {
@@ -261,6 +262,7 @@ __global__ void k_qp_setup(int64_t nc, const int64_t *row_ptr, const int64_t *co
         const double b = volphi[l < nc ? l : l - nc];
         const double w = (eps * b) * (eps * b);
         diag[l] = d + w;
+        exc[l] = w;
         rhs[l] = b - s;
     }
 }
@@ -291,22 +293,25 @@ __global__ void k_qp_kkt(int64_t nc, const int64_t *row_ptr, const int64_t *col_
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Conjugate gradients on (A-hat A-hat^T + W) d = F, Jacobi preconditioner.
-// Every kernel returns at once when the solve has converged, so that batches
-// of iterations can be queued without reading the state back each time.
+// Preconditioned conjugate gradients on (A-hat A-hat^T + W) d = F.  Every
+// kernel returns at once when the solve has converged, so that batches of
+// iterations can be queued without reading the state back each time.
 
-__global__ void k_cg_init(int64_t n2, const double *F, const double *diag, double *d, double *res, double *z,
-                          double *p, double *partials) {
+__global__ void k_copy(int64_t n, const double *in, double *out, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) out[i] = in[i];
+}
+
+// z = res / diag (Jacobi preconditioner)
+__global__ void k_jacobi_precond(int64_t n, const double *diag, const double *res, double *z, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) z[i] = res[i] / diag[i];
+}
+
+__global__ void k_dot(int64_t n, const double *a, const double *b, double *partials, const CgState *st) {
+    if (st && st->converged) return;
     double acc = 0.0;
-    GRID_STRIDE(l, n2) {
-        const double f = F[l];
-        const double zz = f / diag[l];
-        d[l] = 0.0;
-        res[l] = f;
-        z[l] = zz;
-        p[l] = zz;
-        acc += f * zz;
-    }
+    GRID_STRIDE(i, n) acc += a[i] * b[i];
     acc = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -354,34 +359,28 @@ __global__ void k_cg_alpha(const double *partials, int nparts, CgState *st) {
     }
 }
 
-__global__ void k_cg_update(int64_t n2, const double *diag, const double *p, const double *q, double *d, double *res,
-                            double *z, double *partials, const CgState *st) {
+// d += alpha p, res -= alpha q, partial sums of |res|
+__global__ void k_cg_update(int64_t n2, const double *p, const double *q, double *d, double *res, double *partials,
+                            const CgState *st) {
     if (st->converged) return;
     const double alpha = st->alpha;
-    double rz = 0.0, l1 = 0.0;
+    double l1 = 0.0;
     GRID_STRIDE(l, n2) {
         d[l] += alpha * p[l];
         const double r = res[l] - alpha * q[l];
         res[l] = r;
-        const double zz = r / diag[l];
-        z[l] = zz;
-        rz += r * zz;
         l1 += fabs(r);
     }
-    rz = block_sum(rz);
     l1 = block_sum(l1);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rz;
-        partials[2 * blockIdx.x + 1] = l1;
-    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = l1;
 }
 
-__global__ void k_cg_beta(const double *partials, int nparts, CgState *st) {
+__global__ void k_cg_beta(const double *rz_parts, const double *l1_parts, int nparts, CgState *st) {
     if (st->converged) return;
     double rz = 0.0, l1 = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        rz += partials[2 * i];
-        l1 += partials[2 * i + 1];
+        rz += rz_parts[i];
+        l1 += l1_parts[i];
     }
     rz = block_sum(rz);
     l1 = block_sum(l1);
@@ -390,7 +389,7 @@ __global__ void k_cg_beta(const double *partials, int nparts, CgState *st) {
         st->rz = rz;
         st->res_l1 = l1;
         st->iters += 1;
-        if (l1 <= st->target || !(st->pq > 0.0)) st->converged = 1;
+        if (l1 <= st->target || !(st->pq > 0.0) || !(rz > 0.0)) st->converged = 1;
     }
 }
 
@@ -410,6 +409,15 @@ __global__ void k_qp_accumulate(int64_t nc, const int64_t *row_ptr, const int32_
     }
 }
 
+static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z, const CgState *st) {
+    if (amg) {
+        amg_apply(m, m->amg, res, z, st);
+    } else {
+        k_jacobi_precond<<<blocks_for(2 * m->nc), kThreads, 0, m->stream>>>(2 * m->nc, ptr<double>(m->diag), res, z, st);
+        ++m->launches;
+    }
+}
+
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
     const int bl = blocks_for(n2);
@@ -418,17 +426,22 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     double *a2 = ptr<double>(m->a2), *a2c = ptr<double>(m->a2c), *diag = ptr<double>(m->diag);
     double *rhs = ptr<double>(m->rhs), *qx = ptr<double>(m->qx), *y = ptr<double>(m->qy), *F = ptr<double>(m->F);
     double *d = ptr<double>(m->cg_d), *res = ptr<double>(m->cg_r), *z = ptr<double>(m->cg_z);
-    double *p = ptr<double>(m->cg_p), *q = ptr<double>(m->cg_q), *part = ptr<double>(m->partials);
+    double *p = ptr<double>(m->cg_p), *q = ptr<double>(m->cg_q);
+    double *part = ptr<double>(m->partials);
+    double *part_l1 = part + 152 * 64;
+    double *part_rz = part + 2 * 152 * 64;
     DevInfo *di = ptr<DevInfo>(m->dinfo);
     CgState *st = ptr<CgState>(m->cg);
     CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
 
     k_qp_setup<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
-                                      ptr<double>(m->aN), ptr<double>(m->volphi), eps, a2, diag, rhs);
+                                      ptr<double>(m->aN), ptr<double>(m->volphi), eps, a2, diag,
+                                      ptr<double>(m->qexc), rhs);
     k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, ptr<int32_t>(m->csc_src), a2, a2c);
     cudaMemsetAsync(qx, 0, sizeof(double) * nnz, s);
     cudaMemsetAsync(y, 0, sizeof(double) * n2, s);
     m->launches += 2;
+    const bool amg = m->opt.qp_precond == 1 && amg_build(m, m->amg);
 
     int iters = 0, rounds = 0;
     const double target_abs = m->opt.qp_tol * total_volphi(m);
@@ -443,21 +456,27 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         cudaStreamSynchronize(s);
         if (kkt <= target_abs || rounds == m->opt.qp_max_refine || iters >= m->opt.qp_max_iter) break;
         const double inner = fmax(1e-10 * kkt, 0.25 * target_abs);
-        k_cg_init<<<bl, kThreads, 0, s>>>(n2, F, diag, d, res, z, p, part);
-        k_cg_start<<<1, 1024, 0, s>>>(part, bl, inner, st);
-        m->launches += 2;
+        cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
+        k_copy<<<bl, kThreads, 0, s>>>(n2, F, res, nullptr);
+        precondition(m, amg, res, z, nullptr);
+        k_dot<<<bl, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
+        k_cg_start<<<1, 1024, 0, s>>>(part_rz, bl, inner, st);
+        k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
+        m->launches += 4;
         int done = 0;
         while (!done) {
-            const int batch = 32;
+            const int batch = amg ? 8 : 32;
             for (int k = 0; k < batch; ++k) {
                 k_cg_matvec<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
                                                    ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag,
                                                    p, q, part, st);
                 k_cg_alpha<<<1, 1024, 0, s>>>(part, bl, st);
-                k_cg_update<<<bl, kThreads, 0, s>>>(n2, diag, p, q, d, res, z, part, st);
-                k_cg_beta<<<1, 1024, 0, s>>>(part, bl, st);
+                k_cg_update<<<bl, kThreads, 0, s>>>(n2, p, q, d, res, part_l1, st);
+                precondition(m, amg, res, z, st);
+                k_dot<<<bl, kThreads, 0, s>>>(n2, res, z, part_rz, st);
+                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_l1, bl, st);
                 k_cg_pupdate<<<bl, kThreads, 0, s>>>(n2, z, p, st);
-                m->launches += 5;
+                m->launches += 6;
             }
             cudaMemcpyAsync(host_st, st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
@@ -470,6 +489,16 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     }
     *cg_iters = iters;
     *refines = rounds;
+    m->amg_levels = amg ? m->amg.nlev : 0;
+    m->amg_coarsest = amg ? m->amg.levels[m->amg.nlev - 1].n : 0;
+}
+
+void launch_cg_matvec_once(bchar_mesh_t m, CgState *st) {
+    const int64_t nc = m->nc;
+    k_cg_matvec<<<blocks_for(2 * nc), kThreads, 0, m->stream>>>(
+        nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
+        ptr<double>(m->a2), ptr<double>(m->a2c), ptr<double>(m->diag), ptr<double>(m->cg_p), ptr<double>(m->cg_q),
+        ptr<double>(m->partials), st);
 }
 
 // ---------------------------------------------------------------- bounds, column fix, W

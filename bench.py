@@ -124,14 +124,15 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = inputs.workload(args.workload)
+    wl = inputs.workload(args.workload, n=args.n)
     nc = wl.nc
     nsteps = args.warmup + args.steps
     faces_dev = []
     for st in range(nsteps):
         f = wl.faces(st % wl.steps)
         faces_dev.append([torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev) for a in f])
-    opts = bchar.default_options(precision=bchar.FP32_SPLIT if wl.precision == "fp32split" else bchar.FP64)
+    opts = bchar.default_options(precision=bchar.FP32_SPLIT if wl.precision == "fp32split" else bchar.FP64,
+                                 qp_max_iter=args.qp_max_iter)
     mesh = bchar.Mesh(wl.coords, wl.phi, opts)
     cdt = torch.float32 if wl.c_dtype == "f32" else torch.float64
     c = torch.tensor(wl.c0, dtype=cdt, device=dev)
@@ -207,12 +208,18 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"{WORKLOAD}: 1024x1024 stretched tensor mesh (widths U[0.5h,1.5h], seed 1001), "
                                 "phi=1, single vortex x cos(pi t/T), T=1, dt=0.005, disk c0; FP32 tracking and "
                                 "intersections, FP64 sums/scalings/minimisation/update",
-                   "cells": nc, "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
+                   "cells": nc, "cells_per_axis": len(wl.coords[0]) - 1, "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps",
+                   "qp_max_iter": args.qp_max_iter,
+                   "qp_note": "conjugate-gradient budget of the minimisation per step; qp_converged counts the "
+                              "steps that reached the 1e-14 optimality tolerance within it"},
         "gpu_launches": int(statistics.mean(i["kernel_launches"] for i in infos) * args.steps) + 0,
         "roofline": roofline,
         "stage_ms_per_step": {k: round(v, 3) for k, v in per_step_ms.items()},
         "step_stats": {"cg_iters_mean": statistics.mean(i["cg_iters"] for i in infos),
-                       "qp_converged": sum(i["qp_converged"] for i in infos), "nnz": last["nnz"],
+                       "qp_converged": sum(i["qp_converged"] for i in infos),
+                       "kkt_rel_max": max(i["kkt_rel"] for i in infos),
+                       "max_rel_row_res_max": max(i["max_rel_row_res"] for i in infos),
+                       "amg_levels": last["amg_levels"], "nnz": last["nnz"],
                        "substeps": last["substeps"],
                        "max_rel_mass_change": max(abs(i["mass_after"] - i["mass_before"]) / i["mass_before"]
                                                   for i in infos)},
@@ -321,6 +328,8 @@ def main():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--qp-max-iter", type=int, default=1000)
+    p.add_argument("--n", type=int, default=None, help="cells per axis (same recipe; for small profiling runs)")
     args = p.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":

@@ -431,11 +431,21 @@ def minimise(AN: sp.csr_matrix, row_target, col_target, tol: float = 1e-14, pena
     return factor, x, info
 
 
-def column_fix(A: sp.csr_matrix, col_target) -> sp.csr_matrix:
-    """Scale every column to its global target |M_j|_phi, the first half of
-    eq. volAdj, so that eq. globalmassconsMat holds to rounding after the
-    penalised minimisation."""
-    colsum = np.asarray(A.sum(axis=0)).reshape(-1)
+def column_fix(Aq: sp.csr_matrix, AN: sp.csr_matrix, col_target) -> sp.csr_matrix:
+    """Scale every column to its global target |M_j|_phi (the first half of
+    eq. volAdj), so that eq. globalmassconsMat holds to rounding after the
+    minimisation.  A column whose entries were all clipped to zero keeps its
+    A^(N) entries (no scaling could restore it otherwise)."""
+    colsum = np.asarray(Aq.sum(axis=0)).reshape(-1)
+    dead = colsum == 0.0
+    A = Aq.copy()
+    if dead.any():
+        A = A.tocsc()
+        ANc = AN.tocsc()
+        for j in np.flatnonzero(dead):
+            A.data[A.indptr[j]:A.indptr[j + 1]] = ANc.data[ANc.indptr[j]:ANc.indptr[j + 1]]
+        A = A.tocsr()
+        colsum = np.asarray(A.sum(axis=0)).reshape(-1)
     out = (A @ sp.diags(col_target / colsum)).tocsr()
     out.sort_indices()
     return out
@@ -475,7 +485,7 @@ def step(mesh: Mesh, faces, dt: float, c, opts: StepOptions | None = None):
     factor, x, qinfo = minimise(AN, volphi, volphi, opts.qp_tol, opts.penalty)
     Aq = AN.copy()
     Aq.data = AN.data * factor
-    Afin = column_fix(Aq, volphi)
+    Afin = column_fix(Aq, AN, volphi)
     rowsum = np.asarray(Afin.sum(axis=1)).reshape(-1)
     colsum = np.asarray(Afin.sum(axis=0)).reshape(-1)
     qinfo.update({"max_rel_row_res": float(np.max(np.abs(rowsum - volphi) / volphi)),

@@ -518,25 +518,34 @@ __global__ void k_clip(int64_t nc, const int64_t *row_ptr, const double *aN, con
     if (clipped) atomicAdd(&info->n_clipped, clipped);
 }
 
-// C2_j = |M_j|_phi / sum_i a_q,ij (first half of eq. volAdj)
+// C2_j = |M_j|_phi / sum_i a_q,ij (first half of eq. volAdj).  A column whose
+// entries were all clipped to zero keeps its A^(N) entries (dead[j] = 1).
 __global__ void k_colfix(int64_t nc, const int64_t *col_ptr, const int32_t *csc_src, const double *aq,
-                         const double *volphi, double *C2) {
+                         const double *aN, const double *volphi, double *C2, int32_t *dead) {
     GRID_STRIDE(j, nc) {
         double s = 0.0;
         for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) s += aq[csc_src[p]];
-        C2[j] = s > 0.0 ? volphi[j] / s : 1.0;
+        int d = 0;
+        if (s == 0.0) {
+            d = 1;
+            for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) s += aN[csc_src[p]];
+        }
+        dead[j] = d;
+        C2[j] = volphi[j] / s;
     }
 }
 
 // a_KM final, W_KM = a_KM / |K|_phi, and the relative row residual.
-__global__ void k_weights(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aq, const double *C2,
-                          const double *volphi, double *afin, double *wgt, unsigned long long *row_res) {
+__global__ void k_weights(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aq, const double *aN,
+                          const int32_t *dead, const double *C2, const double *volphi, double *afin, double *wgt,
+                          unsigned long long *row_res) {
     double mx = 0.0;
     GRID_STRIDE(i, nc) {
         double s = 0.0;
         const double vi = volphi[i];
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const double a = aq[e] * C2[col[e]];
+            const int32_t j = col[e];
+            const double a = (dead[j] ? aN[e] : aq[e]) * C2[j];
             afin[e] = a;
             wgt[e] = a / vi;
             s += a;
@@ -553,10 +562,12 @@ void launch_finalise(bchar_mesh_t m) {
     DevInfo *di = ptr<DevInfo>(m->dinfo);
     double *aq = ptr<double>(m->a2);  // reuse: a2 is no longer needed
     k_clip<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<double>(m->aN), ptr<double>(m->qx), aq, di);
+    int32_t *dead = ptr<int32_t>(m->colfill);  // scratch: the column fill counters are no longer needed
     k_colfix<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src), aq,
-                                             ptr<double>(m->volphi), ptr<double>(m->C));
-    k_weights<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), aq, ptr<double>(m->C),
-                                              ptr<double>(m->volphi), ptr<double>(m->afin), ptr<double>(m->wgt),
+                                             ptr<double>(m->aN), ptr<double>(m->volphi), ptr<double>(m->C), dead);
+    k_weights<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), aq, ptr<double>(m->aN),
+                                              dead, ptr<double>(m->C), ptr<double>(m->volphi), ptr<double>(m->afin),
+                                              ptr<double>(m->wgt),
                                               reinterpret_cast<unsigned long long *>(&di->max_rel_row_res));
     k_col_error<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
                                                 ptr<double>(m->afin), ptr<double>(m->volphi),

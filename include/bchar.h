@@ -188,6 +188,28 @@ enum {
  * Errors: INVALID_ARG (no step yet, bad stage, reps < 1), CUDA. */
 bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms);
 
+/* The porous mass sum_K |K|_phi c_K (the quantity bchar_step_info reports as
+ * mass_before / mass_after), for callers that must not allocate device memory:
+ * a time-stepping loop with a fixed device-memory budget, a framework that
+ * hands out memory only from its own pool, or code that must not take the
+ * implicit synchronisation of cudaMalloc/cudaFree in the middle of a step.
+ * The paper has no counterpart; this is a service of the library.
+ *   volphi   DEVICE array of n values |K|_phi (FP64), caller-owned
+ *   c        DEVICE array of n values (c_dtype BCHAR_C_F64 or BCHAR_C_F32), caller-owned
+ *   n        1 <= n <= 16 777 216 (2^24); larger n returns BCHAR_ERR_CAPACITY
+ *   mass_out DEVICE pointer to one double, written by the call
+ *   stream   cudaStream_t the work is ordered on (NULL = legacy default)
+ * Allocates nothing: the per-block partial sums use a fixed 8 KB array inside
+ * the library's device memory, held by every GPU that loads the library until
+ * the process exits.  The first call on a device looks up that array's
+ * address (with the device current), so make the first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (different streams, no ordering between them) race and may return wrong
+ * sums; order them on one stream.  Returns when the work is queued.
+ * Errors: INVALID_ARG, CAPACITY, CUDA. */
+bchar_status bchar_mass_noalloc(const double *volphi, const void *c, int c_dtype, int64_t n, double *mass_out,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

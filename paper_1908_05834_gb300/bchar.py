@@ -87,6 +87,9 @@ lib.bchar_time_stage.restype = ctypes.c_int
 
 STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK = 0, 1, 2, 3
 
+lib.bchar_mass_noalloc.argtypes = [_P, _P, ctypes.c_int, _I64, _P, _P]
+lib.bchar_mass_noalloc.restype = ctypes.c_int
+
 bchar_default_options = lib.bchar_default_options
 bchar_create_mesh = lib.bchar_create_mesh
 bchar_set_velocity = lib.bchar_set_velocity
@@ -97,6 +100,7 @@ bchar_last_error = lib.bchar_last_error
 bchar_export_matrix = lib.bchar_export_matrix
 bchar_export_tracked = lib.bchar_export_tracked
 bchar_time_stage = lib.bchar_time_stage
+bchar_mass_noalloc = lib.bchar_mass_noalloc
 
 
 def default_options(**kw) -> Options:

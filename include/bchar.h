@@ -66,7 +66,7 @@ typedef struct {
     double penalty;     /* eps of the penalised minimisation (1e-7), see bchar_step */
     double qp_tol;      /* stop when the L1 optimality residual <= qp_tol * sum |K|_phi (1e-14) */
     int qp_max_iter;    /* cap on conjugate-gradient iterations per solve (200000) */
-    int qp_max_refine;  /* cap on refinement rounds (30) */
+    int qp_max_refine;  /* cap on refinement rounds (60) */
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
     int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
                            1 = aggregation multigrid (default), 0 = Jacobi */
@@ -91,6 +91,7 @@ typedef struct {
     int32_t kernel_launches; /* kernels launched by this call */
     int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
     int32_t amg_coarsest;    /* unknowns on its coarsest level */
+    int32_t unbalanced;      /* connected components whose local targets were rescaled (see bchar_step) */
 } bchar_step_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -128,7 +129,11 @@ bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int
  *      classical RK4 (Sec 2 eq. charac, Sec 3 eq. rTrackedBall);
  *   2. a^(0)_KM = V_{K,M} from the closed-form ball intersections
  *      (Sec 3.1, eq. fracMaterial, eq. ball_int);
- *   3. N alternating column/row scalings (Sec 3.2, eq. volAdj);
+ *   3. consistent targets: on a connected component of A's pattern whose
+ *      local targets sum_rows |K_i|_phi differ from its global ones
+ *      sum_cols |M_j|_phi (the balls can cause this), the local targets are
+ *      scaled by their ratio; then N alternating column/row scalings
+ *      (Sec 3.2, eq. volAdj);
  *   4. the minimisation of Sec 3.2 (eq. opti_masscons), read as: the
  *      penalised minimum-norm adjustment x of min 1/2 x.x + 1/2 sum (s/(eps b))^2
  *      (s the 2 n_c constraint residuals), then 1 + x clipped to the paper's

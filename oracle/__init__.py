@@ -12,6 +12,7 @@ the paper's order and notation, in double precision:
 * tracking the ball centres along the flow (Sec 2 eq. charac; Sec 3)
 * tracked radius (Sec 3, eq. ball_volChange / eq. rTrackedBall)
 * initial weights V_{K,M}                   (Sec 3.1, eq. fracMaterial, eq. ball_int)
+* consistent local targets per component    (Sec 3.2, eq. localmassconsMat / globalmassconsMat)
 * alternating column/row scaling, N times   (Sec 3.2, eq. volAdj)
 * the matrix A-hat and the minimisation     (Sec 3.2, eq. opti_masscons)
 * a final column scaling                    (Sec 3.2, first half of eq. volAdj)
@@ -31,6 +32,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.csgraph as csgraph
 import scipy.sparse.linalg as spla
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -342,6 +344,47 @@ def initial_matrix(mesh: Mesh, faces, dt: float, substeps: int, drop_tol: float 
     return A0, {"void_balls": voids, "empty_cols": n_empty, "ball_offset": offset, "centres": centres, "rhat": rhat}
 
 
+def balanced_targets(A0: sp.csr_matrix, volphi: np.ndarray, tol: float = 1e-12, theta: float = 1e-3):
+    """Local targets made consistent with the global ones (reading).
+
+    eq. localmassconsMat and eq. globalmassconsMat can hold together only if,
+    on every connected block of rows and columns, the sum of |K_i|_phi over
+    its rows equals the sum of |M_j|_phi over its columns.  The balls can
+    break this on stretched or porous meshes.  Blocks are the connected
+    components of the graph linking row i to column j when
+    a_ij >= theta * max(largest entry of row i, largest entry of column j):
+    a sliver overlap below that share cannot carry a block's mismatch (it
+    would need 1 + x far outside the bounds 0 <= 1 + x <= 2).  On a block with
+    relative mismatch > tol the row targets are multiplied by
+    sum_cols / sum_rows: global mass conservation stays exact and local
+    conservation is relaxed by that factor there only.
+    Returns (b_loc, number of rescaled blocks)."""
+    n = A0.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A0.indptr))
+    rowmax = np.asarray(A0.max(axis=1).todense()).reshape(-1)
+    colmax = np.asarray(A0.max(axis=0).todense()).reshape(-1)
+    strong = A0.data >= theta * np.maximum(rowmax[rows], colmax[A0.indices])
+    G = sp.csr_matrix((np.ones(int(strong.sum())), (rows[strong], A0.indices[strong] + n)), shape=(2 * n, 2 * n))
+    ncomp, labels = csgraph.connected_components(G, directed=False)
+    sum_rows = np.zeros(ncomp)
+    sum_cols = np.zeros(ncomp)
+    for lab, grp in _groups(labels[:n]):
+        sum_rows[lab] = math.fsum(volphi[grp].tolist())
+    for lab, grp in _groups(labels[n:]):
+        sum_cols[lab] = math.fsum(volphi[grp].tolist())
+    bad = np.abs(sum_cols - sum_rows) > tol * sum_rows
+    factor = np.where(bad, sum_cols / np.where(sum_rows > 0, sum_rows, 1.0), 1.0)
+    return volphi * factor[labels[:n]], int(np.sum(bad))
+
+
+def _groups(labels: np.ndarray):
+    order = np.argsort(labels, kind="stable")
+    cuts = np.flatnonzero(np.diff(labels[order])) + 1
+    for grp in np.split(order, cuts):
+        if grp.size:
+            yield int(labels[grp[0]]), grp
+
+
 # ---------------------------------------------------------------- scaling
 
 
@@ -479,10 +522,11 @@ def step(mesh: Mesh, faces, dt: float, c, opts: StepOptions | None = None):
     s = opts.substeps or substep_count(mesh, faces, dt, opts.cfl)
     volphi = mesh.volphi()
     A0, ainfo = initial_matrix(mesh, faces, dt, s, opts.drop_tol)
-    AN = scale(A0, volphi, volphi, opts.n_scale)
+    b_loc, n_unbal = balanced_targets(A0, volphi)
+    AN = scale(A0, b_loc, volphi, opts.n_scale)
     colsum = np.asarray(AN.sum(axis=0)).reshape(-1)
     scale_err = float(np.max(np.abs(colsum - volphi) / volphi))
-    factor, x, qinfo = minimise(AN, volphi, volphi, opts.qp_tol, opts.penalty)
+    factor, x, qinfo = minimise(AN, b_loc, volphi, opts.qp_tol, opts.penalty)
     Aq = AN.copy()
     Aq.data = AN.data * factor
     Afin = column_fix(Aq, AN, volphi)
@@ -497,5 +541,5 @@ def step(mesh: Mesh, faces, dt: float, c, opts: StepOptions | None = None):
     return {
         "substeps": s, "A0": A0, "AN": AN, "Aq": Aq, "A": Afin, "W": W, "x": x, "factor": factor,
         "c": c_new, "mass_before": total_mass(mesh, c), "mass_after": total_mass(mesh, c_new),
-        "scale_err": scale_err, **{k: v for k, v in ainfo.items()}, **qinfo,
+        "scale_err": scale_err, "b_loc": b_loc, "unbalanced": n_unbal, **{k: v for k, v in ainfo.items()}, **qinfo,
     }

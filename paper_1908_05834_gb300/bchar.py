@@ -38,7 +38,7 @@ class StepInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("substeps", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
                 ("refines", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
                 ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32)]
+                ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

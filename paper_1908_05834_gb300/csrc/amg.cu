@@ -10,8 +10,9 @@
 // links handles both:
 //   - each level pairs every node with its heaviest neighbour when the choice
 //     is mutual (kHandshakes rounds, each among the nodes still unpaired);
-//     unpaired nodes stay single, and coarsening stops when a level would
-//     keep more than kStall of its nodes;
+//     a node left unpaired joins the aggregate of its heaviest neighbour when
+//     that one is paired, else stays single; coarsening stops when a level
+//     would keep more than kStall of its nodes;
 //   - the coarse operator is the Galerkin product P^T L P for the piecewise-
 //     constant P of the aggregates (coarse edge = sum of fine edges between
 //     two aggregates).  Its diagonal is formed as the coarse node's excess
@@ -106,24 +107,59 @@ __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
     }
 }
 
-__global__ void k_leaders(int64_t n, const int32_t *partner, int32_t *is_leader) {
+// Leader of every node: the smaller node of a pair; an unpaired node whose
+// heaviest neighbour (first round) is paired joins that pair's aggregate,
+// otherwise it stays single.  Attaching only to paired nodes leaves no chains.
+__global__ void k_leaders(int64_t n, const int32_t *partner, const int32_t *heaviest, int32_t *leader,
+                          int32_t *is_leader, int *isolated) {
     GRID_STRIDE(i, n) {
+        if (heaviest[i] < 0 && partner[i] < 0) atomicAdd(isolated, 1);  // no neighbour at all
         const int32_t p = partner[i];
-        is_leader[i] = (p < 0 || i < p) ? 1 : 0;
+        int32_t lead;
+        if (p >= 0) {
+            lead = i < p ? static_cast<int32_t>(i) : p;
+        } else {
+            const int32_t t = heaviest[i];
+            if (t >= 0 && partner[t] >= 0) {
+                const int32_t q = partner[t];
+                lead = t < q ? t : q;
+            } else {
+                lead = static_cast<int32_t>(i);
+            }
+        }
+        leader[i] = lead;
+        is_leader[i] = lead == i ? 1 : 0;
     }
 }
 
-// agg[i] = coarse index of i's aggregate; members[2 I + {0,1}] its nodes.
-__global__ void k_aggregates(int64_t n, const int32_t *partner, const int64_t *leader_pos, int32_t *agg,
-                             int32_t *members) {
+__global__ void k_aggregates(int64_t n, const int32_t *leader, const int64_t *leader_pos, int32_t *agg,
+                             int32_t *count) {
     GRID_STRIDE(i, n) {
-        const int32_t p = partner[i];
-        const int64_t lead = (p < 0 || i < p) ? i : p;
-        const int64_t I = leader_pos[lead];
-        agg[i] = static_cast<int32_t>(I);
-        if (lead == i) {
-            members[2 * I] = static_cast<int32_t>(i);
-            members[2 * I + 1] = p;  // -1 for a single node
+        const int32_t I = static_cast<int32_t>(leader_pos[leader[i]]);
+        agg[i] = I;
+        atomicAdd(&count[I], 1);
+    }
+}
+
+__global__ void k_members_fill(int64_t n, const int32_t *agg, const int64_t *mptr, int32_t *fill, int32_t *mlist) {
+    GRID_STRIDE(i, n) {
+        const int32_t I = agg[i];
+        mlist[mptr[I] + atomicAdd(&fill[I], 1)] = static_cast<int32_t>(i);
+    }
+}
+
+// Members of each aggregate in increasing node order (small insertion sort).
+__global__ void k_members_sort(int64_t nco, const int64_t *mptr, int32_t *mlist) {
+    GRID_STRIDE(I, nco) {
+        const int64_t b = mptr[I], e = mptr[I + 1];
+        for (int64_t p = b + 1; p < e; ++p) {
+            const int32_t v = mlist[p];
+            int64_t q = p;
+            while (q > b && mlist[q - 1] > v) {
+                mlist[q] = mlist[q - 1];
+                --q;
+            }
+            mlist[q] = v;
         }
     }
 }
@@ -133,14 +169,13 @@ __global__ void k_aggregates(int64_t n, const int32_t *partner, const int64_t *l
 // Collect, sort and merge the coarse neighbours of coarse node I (internal
 // edges drop out of the Laplacian).  Returns the number of distinct
 // neighbours (or -1 on overflow); *eI receives the coarse excess.
-__device__ int coarse_row(int64_t I, const int32_t *members, const int64_t *ptr, const int32_t *col,
-                          const double *val, const double *exc, const int32_t *agg, int32_t *cbuf, double *vbuf,
-                          double *eI) {
+__device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
+                          const int32_t *col, const double *val, const double *exc, const int32_t *agg, int32_t *cbuf,
+                          double *vbuf, double *eI) {
     int cnt = 0;
     double e_sum = 0.0;
-    for (int k = 0; k < 2; ++k) {
-        const int32_t m = members[2 * I + k];
-        if (m < 0) continue;
+    for (int64_t k = mptr[I]; k < mptr[I + 1]; ++k) {
+        const int32_t m = mlist[k];
         e_sum += exc[m];
         for (int64_t e = ptr[m]; e < ptr[m + 1]; ++e) {
             const int32_t J = agg[col[e]];
@@ -166,14 +201,14 @@ __device__ int coarse_row(int64_t I, const int32_t *members, const int64_t *ptr,
     return cnt;
 }
 
-__global__ void k_coarse_count(int64_t nco, const int32_t *members, const int64_t *ptr, const int32_t *col,
-                               const double *val, const double *exc, const int32_t *agg, int32_t *rowcnt,
-                               int *overflow) {
+__global__ void k_coarse_count(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
+                               const int32_t *col, const double *val, const double *exc, const int32_t *agg,
+                               int32_t *rowcnt, int *overflow) {
     int32_t cbuf[kCoarseCap];
     double vbuf[kCoarseCap];
     GRID_STRIDE(I, nco) {
         double e;
-        const int c = coarse_row(I, members, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
         if (c < 0) {
             atomicOr(overflow, 1);
             rowcnt[I] = 0;
@@ -183,14 +218,14 @@ __global__ void k_coarse_count(int64_t nco, const int32_t *members, const int64_
     }
 }
 
-__global__ void k_coarse_fill(int64_t nco, const int32_t *members, const int64_t *ptr, const int32_t *col,
-                              const double *val, const double *exc, const int32_t *agg, const int64_t *cptr,
-                              int32_t *ccol, double *cval, double *cdiag, double *cexc) {
+__global__ void k_coarse_fill(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
+                              const int32_t *col, const double *val, const double *exc, const int32_t *agg,
+                              const int64_t *cptr, int32_t *ccol, double *cval, double *cdiag, double *cexc) {
     int32_t cbuf[kCoarseCap];
     double vbuf[kCoarseCap];
     GRID_STRIDE(I, nco) {
         double e;
-        const int c = coarse_row(I, members, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
         const int64_t dst = cptr[I];
         double d = e;
         for (int k = 0; k < c; ++k) {
@@ -238,11 +273,13 @@ __global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, cons
     }
 }
 
-__global__ void k_restrict(int64_t nco, const int32_t *members, const double *r, double *bc, const CgState *st) {
+__global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlist, const double *r, double *bc,
+                           const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(I, nco) {
-        const int32_t m1 = members[2 * I + 1];
-        bc[I] = r[members[2 * I]] + (m1 >= 0 ? r[m1] : 0.0);
+        double s = 0.0;
+        for (int64_t k = mptr[I]; k < mptr[I + 1]; ++k) s += r[mlist[k]];
+        bc[I] = s;
     }
 }
 
@@ -274,7 +311,7 @@ __global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, co
 
 void amg_release(Amg &amg) {
     for (AmgLevel &L : amg.levels) {
-        Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.members, &L.x, &L.x2, &L.b, &L.r};
+        Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.mptr, &L.mlist, &L.x, &L.x2, &L.b, &L.r};
         for (Buf *b : all) release(*b);
     }
     amg.levels.clear();
@@ -308,34 +345,40 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
                                                         ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
                                                         ptr<double>(L0.val));
     m->launches += 2;
-    if (!ensure(m, amg.tmp, sizeof(int32_t) * 3 * L0.n + 64)) return false;
     while (amg.nlev < kMaxLevels) {
         AmgLevel &F = amg.levels[amg.nlev - 1];
         if (F.n <= kCoarsest) break;
         const double *fexc = F.exc_ext ? F.exc_ext : ptr<double>(F.exc);
-        if (!ensure(m, amg.tmp, sizeof(int32_t) * 3 * F.n + 64) || !ensure(m, F.agg, sizeof(int32_t) * F.n))
+        if (!ensure(m, amg.tmp, sizeof(int32_t) * 5 * F.n + 64) || !ensure(m, F.agg, sizeof(int32_t) * F.n))
             return false;
         int32_t *best = ptr<int32_t>(amg.tmp);
         int32_t *partner = best + F.n;
-        int32_t *lead = partner + F.n;
-        int *overflow = reinterpret_cast<int *>(lead + F.n);
+        int32_t *heavy = partner + F.n;   // heaviest neighbour of the first round
+        int32_t *leader = heavy + F.n;
+        int32_t *flag = leader + F.n;     // leader flags, later member counts / fill / row counts
+        int *overflow = reinterpret_cast<int *>(flag + F.n);
+        int *isolated = overflow + 1;
         const int bl = blocks_for(F.n);
         cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * F.n, s);
-        cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        cudaMemsetAsync(overflow, 0, 2 * sizeof(int), s);
         for (int round = 0; round < kHandshakes; ++round) {
             k_heaviest<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
-                                               partner, round > 0, best);
-            k_handshake<<<bl, kThreads, 0, s>>>(F.n, best, partner);
+                                               partner, round > 0, round == 0 ? heavy : best);
+            k_handshake<<<bl, kThreads, 0, s>>>(F.n, round == 0 ? heavy : best, partner);
             m->launches += 2;
         }
-        k_leaders<<<bl, kThreads, 0, s>>>(F.n, partner, lead);
+        k_leaders<<<bl, kThreads, 0, s>>>(F.n, partner, heavy, leader, flag, isolated);
         // leader positions: scan of the leader flags (int32 -> int64), reuse the
-        // per-level x buffer as int64 scratch (n + 1 entries fit in x and x2)
+        // per-level x buffer as int64 scratch (it holds n + 1 entries)
         int64_t *pos = reinterpret_cast<int64_t *>(ptr<double>(F.x));
-        scan_i32_to_i64(m, lead, pos, F.n);
+        scan_i32_to_i64(m, flag, pos, F.n);
         int64_t nco = 0;
+        int niso = 0;
         cudaMemcpyAsync(&nco, pos + F.n, sizeof nco, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&niso, isolated, sizeof niso, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        m->launches += 1;
+        (void)niso;
         if (nco >= F.n * kStall || nco < 1) break;  // matching stalled: this is the coarsest level
         if (static_cast<int>(amg.levels.size()) <= amg.nlev) amg.levels.resize(amg.nlev + 1);
         AmgLevel &Fr = amg.levels[amg.nlev - 1];  // re-fetch after resize
@@ -343,13 +386,22 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         C.n = nco;
         C.diag_ext = nullptr;
         C.exc_ext = nullptr;
-        if (!ensure(m, C.members, sizeof(int32_t) * 2 * nco) || !ensure(m, C.ptr, sizeof(int64_t) * (nco + 1)) ||
-            !ensure(m, C.diag, sizeof(double) * nco) || !ensure(m, C.exc, sizeof(double) * nco) ||
-            !level_vectors(m, C))
+        if (!ensure(m, C.mptr, sizeof(int64_t) * (nco + 1)) || !ensure(m, C.mlist, sizeof(int32_t) * Fr.n) ||
+            !ensure(m, C.ptr, sizeof(int64_t) * (nco + 1)) || !ensure(m, C.diag, sizeof(double) * nco) ||
+            !ensure(m, C.exc, sizeof(double) * nco) || !level_vectors(m, C))
             return false;
-        k_aggregates<<<bl, kThreads, 0, s>>>(Fr.n, partner, pos, ptr<int32_t>(Fr.agg), ptr<int32_t>(C.members));
-        int32_t *rowcnt = lead;  // the leader flags are no longer needed
-        k_coarse_count<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int32_t>(C.members), ptr<int64_t>(Fr.ptr),
+        // aggregates: map, member counts -> pointers, members sorted by node
+        cudaMemsetAsync(flag, 0, sizeof(int32_t) * nco, s);
+        k_aggregates<<<bl, kThreads, 0, s>>>(Fr.n, leader, pos, ptr<int32_t>(Fr.agg), flag);
+        scan_i32_to_i64(m, flag, ptr<int64_t>(C.mptr), nco);
+        cudaMemsetAsync(flag, 0, sizeof(int32_t) * nco, s);
+        k_members_fill<<<bl, kThreads, 0, s>>>(Fr.n, ptr<int32_t>(Fr.agg), ptr<int64_t>(C.mptr), flag,
+                                               ptr<int32_t>(C.mlist));
+        k_members_sort<<<blocks_for(nco), kThreads, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
+        m->launches += 3;
+        int32_t *rowcnt = flag;
+        k_coarse_count<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
+                                                            ptr<int64_t>(Fr.ptr),
                                                             ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
                                                             ptr<int32_t>(Fr.agg), rowcnt, overflow);
         scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
@@ -364,7 +416,8 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
             !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
             return false;
-        k_coarse_fill<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int32_t>(C.members), ptr<int64_t>(Fr.ptr),
+        k_coarse_fill<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
+                                                           ptr<int64_t>(Fr.ptr),
                                                            ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
                                                            ptr<int32_t>(Fr.agg), ptr<int64_t>(C.ptr),
                                                            ptr<int32_t>(C.col), ptr<double>(C.val),
@@ -394,7 +447,7 @@ void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgS
         k_jacobi0<<<bl, kThreads, 0, s>>>(L.n, level_diag(L), ptr<double>(L.b), ptr<double>(L.x), st);
         k_residual<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
                                            level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.r), st);
-        k_restrict<<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int32_t>(C.members), ptr<double>(L.r),
+        k_restrict<<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<double>(L.r),
                                                         ptr<double>(C.b), st);
         m->launches += 3;
     }

@@ -127,7 +127,7 @@ void bchar_default_options(bchar_options *o) {
     o->penalty = 1e-7;
     o->qp_tol = 1e-14;
     o->qp_max_iter = 200000;
-    o->qp_max_refine = 30;
+    o->qp_max_refine = 60;
     o->div_tol = 1e-9;
     o->qp_precond = 1;
 }
@@ -158,7 +158,7 @@ void bchar_destroy(bchar_mesh_t m) {
     Buf *all[] = {&m->phi, &m->phif, &m->volphi, &m->rad, &m->radf, &m->rhophi, &m->rhophif, &m->cnt,
                   &m->ball_off, &m->ball_cell, &m->t_cell, &m->t_xi, &m->t_rhat, &m->slab_col, &m->slab_val,
                   &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
-                  &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->a2,
+                  &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->bloc, &m->uf_parent, &m->uf_label, &m->comp_acc, &m->a2,
                   &m->a2c, &m->diag, &m->qexc, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
                   &m->cg_q, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
     for (Buf *b : all) release(*b);
@@ -206,11 +206,13 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
         if (!(phi[k] > 0.0)) return BCHAR_ERR_INVALID_ARG;
         if (phi[k] != phi[0]) phi_const = false;
     }
+    double max_vp = 0.0;
     for (int64_t k = 0; k < nc; ++k) {
         int64_t c[3] = {k % n[0], (k / n[0]) % n[1], k / (n[0] * n[1])};
         double v = phi[k];
         for (int a = 0; a < dim; ++a) v *= coords[a][c[a] + 1] - coords[a][c[a]];
         sum_vp += v;
+        max_vp = v > max_vp ? v : max_vp;
     }
 
     bchar_mesh_t m = new bchar_mesh_s();
@@ -223,6 +225,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
     m->phi_const = phi_const;
     m->hmin = hmin;
     m->sum_volphi = sum_vp;
+    m->max_volphi = max_vp * (1.0 + 1e-12);  // a bound on the device's |K|_phi (same product, maybe another order)
 
     bool ok = true;
     for (int a = 0; a < dim; ++a) {
@@ -241,6 +244,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
          ensure(m, m->colfill, sizeof(int32_t) * nc) && ensure(m, m->row_len, sizeof(int32_t) * nc) &&
          ensure(m, m->row_ptr, sizeof(int64_t) * (nc + 1)) && ensure(m, m->col_ptr, sizeof(int64_t) * (nc + 1)) &&
          ensure(m, m->R, sizeof(double) * nc) && ensure(m, m->C, sizeof(double) * nc) &&
+         ensure(m, m->bloc, sizeof(double) * nc) &&
          ensure(m, m->seeds, sizeof(unsigned long long) * kMaxSeeds) &&
          ensure(m, m->diag, sizeof(double) * 2 * nc) && ensure(m, m->rhs, sizeof(double) * 2 * nc) &&
          ensure(m, m->qexc, sizeof(double) * 2 * nc) &&
@@ -417,6 +421,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         return BCHAR_ERR_OUT_OF_MEMORY;
     launch_compact(m);
     launch_transpose(m);
+    if (!launch_balance(m)) return BCHAR_ERR_OUT_OF_MEMORY;
 
     // N alternating scalings, the minimisation, bounds and column fix, update
     launch_scaling(m);
@@ -426,6 +431,11 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     launch_update(m, c_in, c_out, c_dtype);
     cudaEventRecord(ev1, m->stream);
     if ((st = read_info(m)) != BCHAR_OK) return st;
+    if (h->err) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "capacity error bits 0x%x", h->err);
+        return fail(m, BCHAR_ERR_CAPACITY, msg);
+    }
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
@@ -453,6 +463,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->kernel_launches = m->launches;
         info->amg_levels = m->amg_levels;
         info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);
+        info->unbalanced = h->unbalanced;
     }
     (void)ms;
     return BCHAR_OK;

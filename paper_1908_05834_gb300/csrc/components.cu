@@ -1,0 +1,140 @@
+// Consistent local targets (reading of Sec 3.2): the row targets |K_i|_phi
+// of a connected block of rows and columns are multiplied by
+// sum_cols |M_j|_phi / sum_rows |K_i|_phi when the two sums differ by more
+// than 1e-12 relative, so that the constraints of eq. localmassconsMat and
+// eq. globalmassconsMat can hold together.  Row i and column j are linked
+// when a0_ij >= theta * max(largest entry of row i, largest entry of
+// column j), theta = 1e-3: a sliver overlap below that share cannot carry a
+// block's mismatch within the bounds 0 <= 1 + x <= 2.
+//
+// Components: lock-free union-find over the 2 n_c row/column nodes, always
+// hooking the larger root under the smaller one, so every component ends with
+// its smallest node as root whatever the order of the unions.
+// Sums: |K|_phi is converted to an exact 52-bit fixed-point integer (scaled by
+// a power of two fixed per mesh) split into two 26-bit limbs whose integer
+// sums cannot overflow, so the per-component sums do not depend on the order
+// of the atomic additions (the step stays bitwise reproducible).
+#include <math.h>
+
+#include "device.cuh"
+
+namespace bchar {
+
+#define GRID_STRIDE(i, n)                                                                    \
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < (n); \
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
+constexpr int kUnionRetries = 1 << 20;
+constexpr double kTheta = 1e-3;
+
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
+    for (int it = 0; it < kUnionRetries; ++it) {
+        const int32_t p = parent[x];
+        if (p == x) return x;
+        const int32_t g = parent[p];
+        if (g != p) parent[x] = g;  // path halving; a stale value is still an ancestor
+        x = g;
+    }
+    return x;
+}
+
+__global__ void k_uf_init(int64_t n2, int32_t *parent) {
+    GRID_STRIDE(l, n2) parent[l] = static_cast<int32_t>(l);
+}
+
+// Largest entry of every column of A^(0).
+__global__ void k_colmax(int64_t nc, const int64_t *col_ptr, const int32_t *csc_src, const double *a0, double *cmax) {
+    GRID_STRIDE(j, nc) {
+        double mx = 0.0;
+        for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) mx = fmax(mx, a0[csc_src[p]]);
+        cmax[j] = mx;
+    }
+}
+
+__global__ void k_uf_union(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a0,
+                           const double *cmax, int32_t *parent, DevInfo *info) {
+    GRID_STRIDE(i, nc) {
+        double rmax = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) rmax = fmax(rmax, a0[e]);
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (a0[e] < kTheta * fmax(rmax, cmax[col[e]])) continue;  // a sliver: does not link the blocks
+            int32_t a = static_cast<int32_t>(i), b = static_cast<int32_t>(nc + col[e]);
+            int it = 0;
+            for (; it < kUnionRetries; ++it) {
+                int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+                if (ra == rb) break;
+                if (ra < rb) {
+                    const int32_t t = ra;
+                    ra = rb;
+                    rb = t;
+                }
+                if (atomicCAS(&parent[ra], ra, rb) == ra) break;
+            }
+            if (it == kUnionRetries) atomicOr(&info->err, kErrUnion);
+        }
+    }
+}
+
+__global__ void k_uf_label(int64_t n2, int32_t *parent, int32_t *label) {
+    GRID_STRIDE(l, n2) label[l] = uf_find(parent, static_cast<int32_t>(l));
+}
+
+// Node l < n_c is row l, node n_c + j column j; both carry |.|_phi of their cell.
+__global__ void k_comp_sums(int64_t nc, const int32_t *label, const double *volphi, int shift,
+                            unsigned long long *acc) {
+    GRID_STRIDE(l, 2 * nc) {
+        const double b = volphi[l < nc ? l : l - nc];
+        const unsigned long long q = static_cast<unsigned long long>(ldexp(b, shift));  // < 2^52, exact
+        const int64_t slot = 4 * static_cast<int64_t>(label[l]) + (l < nc ? 0 : 2);
+        atomicAdd(&acc[slot], q >> 26);
+        atomicAdd(&acc[slot + 1], q & ((1ull << 26) - 1));
+    }
+}
+
+__device__ __forceinline__ double limbs(const unsigned long long *a, int shift) {
+    return ldexp(ldexp(static_cast<double>(a[0]), 26) + static_cast<double>(a[1]), -shift);
+}
+
+__global__ void k_balance(int64_t nc, const int32_t *label, const double *volphi, const unsigned long long *acc,
+                          int shift, double tol, double *bloc, DevInfo *info) {
+    GRID_STRIDE(i, nc) {
+        const int32_t r = label[i];
+        const double sr = limbs(acc + 4 * static_cast<int64_t>(r), shift);
+        const double sc = limbs(acc + 4 * static_cast<int64_t>(r) + 2, shift);
+        double f = 1.0;
+        if (fabs(sc - sr) > tol * sr) {
+            f = sc / sr;
+            if (r == i) atomicAdd(&info->unbalanced, 1);  // one count per component (its root row)
+        }
+        bloc[i] = volphi[i] * f;
+    }
+}
+
+bool launch_balance(bchar_mesh_t m) {
+    const int64_t nc = m->nc, n2 = 2 * nc;
+    if (!ensure(m, m->uf_parent, sizeof(int32_t) * n2) || !ensure(m, m->uf_label, sizeof(int32_t) * n2) ||
+        !ensure(m, m->comp_acc, sizeof(unsigned long long) * 4 * n2))
+        return false;
+    int32_t *parent = ptr<int32_t>(m->uf_parent), *label = ptr<int32_t>(m->uf_label);
+    unsigned long long *acc = ptr<unsigned long long>(m->comp_acc);
+    DevInfo *di = ptr<DevInfo>(m->dinfo);
+    cudaStream_t s = m->stream;
+    int e = 0;
+    frexp(m->max_volphi, &e);                 // max |K|_phi < 2^e
+    const int shift = 52 - e;                 // so every |K|_phi * 2^shift < 2^52
+    cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4 * n2, s);
+    double *cmax = ptr<double>(m->C);  // scratch: the scaling factors are written later
+    k_colmax<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
+                                                 ptr<double>(m->a0), cmax);
+    k_uf_init<<<blocks_for(n2), kThreads, 0, s>>>(n2, parent);
+    k_uf_union<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                                                   ptr<double>(m->a0), cmax, parent, di);
+    k_uf_label<<<blocks_for(n2), kThreads, 0, s>>>(n2, parent, label);
+    k_comp_sums<<<blocks_for(n2), kThreads, 0, s>>>(nc, label, ptr<double>(m->volphi), shift, acc);
+    k_balance<<<blocks_for(nc), kThreads, 0, s>>>(nc, label, ptr<double>(m->volphi), acc, shift, 1e-12,
+                                                  ptr<double>(m->bloc), di);
+    m->launches += 6;
+    return true;
+}
+
+}  // namespace bchar

@@ -25,6 +25,7 @@ enum : int {
     kErrWindow = 4,         // a candidate window is larger than the window limit
     kErrSeeds = 8,          // more than kMaxSeeds empty columns
     kErrSeedCapacity = 16,  // a seeded row overflowed the slab row capacity
+    kErrUnion = 32,         // the component search did not settle (never expected)
 };
 
 // Read-only mesh data passed by value to kernels.
@@ -69,6 +70,7 @@ struct DevInfo {
     int void_balls;
     int n_seeds;
     int n_clipped;
+    int unbalanced;
     long long nnz;
 };
 
@@ -86,11 +88,12 @@ struct Buf {
 };
 
 // One level of the multigrid hierarchy: a symmetric CSR operator (off-diagonal
-// entries only) with its diagonal, the map to the next coarser level and the
-// members of each of its aggregates, plus work vectors.
+// entries only) with its diagonal and excess, the map to the next coarser
+// level, the members of each of its own nodes' aggregates (coarse levels),
+// plus work vectors.
 struct AmgLevel {
     int64_t n = 0, nnz = 0;
-    Buf ptr, col, val, diag, exc, agg, members, x, x2, b, r;
+    Buf ptr, col, val, diag, exc, agg, mptr, mlist, x, x2, b, r;  // mptr/mlist: members of each aggregate
     const double *diag_ext = nullptr;  // level 0 shares the minimisation's diagonal
     const double *exc_ext = nullptr;   // and its excess (the penalty shift)
 };
@@ -114,6 +117,7 @@ struct bchar_mesh_s {
     double hmin = 0.0;
     double r_max = 0.0;
     double sum_volphi = 0.0;
+    double max_volphi = 0.0;
     bchar_options opt{};
     cudaStream_t stream = nullptr;
     std::string err;
@@ -134,7 +138,8 @@ struct bchar_mesh_s {
     bchar::Buf row_ptr, col_ptr;                     // CSR / CSC pointers
     bchar::Buf col, a0, aN, afin, wgt;               // CSR entries
     bchar::Buf csc_row, csc_src;                     // CSC: row and CSR index of each entry
-    bchar::Buf R, C;                                 // scaling factors
+    bchar::Buf R, C, bloc;                           // scaling factors, balanced row targets
+    bchar::Buf uf_parent, uf_label, comp_acc;        // components of A's pattern
     bchar::Buf a2, a2c, diag, qexc, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
     bchar::Buf scan_tmp, partials, dinfo, cg;        // scratch
     bchar::Buf info_host;                            // pinned DevInfo
@@ -183,6 +188,7 @@ VelView vel_view(bchar_mesh_t m);
 // sparse.cu
 void scan_i32_to_i64(bchar_mesh_t m, const int32_t *in, int64_t *out, int64_t n);  // out has n + 1 entries
 void launch_transpose(bchar_mesh_t m);
+bool launch_balance(bchar_mesh_t m);  // components.cu
 void launch_scaling(bchar_mesh_t m);
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines);
 void launch_finalise(bchar_mesh_t m);

@@ -17,6 +17,8 @@
 // All sums run in a fixed order (no floating-point atomics), so a step is
 // bitwise reproducible.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "amg.cuh"
 #include "device.cuh"
@@ -177,13 +179,13 @@ __global__ void k_colscale(int64_t nc, const int64_t *col_ptr, const int32_t *cs
     }
 }
 
-// a^{n+1}: R_i = |K_i|_phi / sum_j a0_ij C_j
+// a^{n+1}: R_i = b_i / sum_j a0_ij C_j, b_i the (balanced) local target
 __global__ void k_rowscale(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a0,
-                           const double *C, const double *volphi, double *R) {
+                           const double *C, const double *brow, double *R) {
     GRID_STRIDE(i, nc) {
         double s = 0.0;
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += a0[e] * C[col[e]];
-        R[i] = volphi[i] / s;
+        R[i] = brow[i] / s;
     }
 }
 
@@ -217,7 +219,7 @@ void launch_scaling(bchar_mesh_t m) {
                                                    ptr<int32_t>(m->csc_src), ptr<double>(m->a0), ptr<double>(m->R),
                                                    ptr<double>(m->volphi), ptr<double>(m->C));
         k_rowscale<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                   ptr<double>(m->a0), ptr<double>(m->C), ptr<double>(m->volphi),
+                                                   ptr<double>(m->a0), ptr<double>(m->C), ptr<double>(m->bloc),
                                                    ptr<double>(m->R));
         m->launches += 2;
     }
@@ -240,8 +242,8 @@ void launch_scaling(bchar_mesh_t m) {
 // Node l < n: row l; node l >= n: column l - n.  b_l = |K|_phi resp. |M|_phi,
 // w_l = (eps b_l)^2.
 __global__ void k_qp_setup(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
-                           const double *aN, const double *volphi, double eps, double *a2, double *diag,
-                           double *exc, double *rhs) {
+                           const double *aN, const double *brow, const double *volphi, double eps, double *a2,
+                           double *diag, double *exc, double *rhs) {
     GRID_STRIDE(l, 2 * nc) {
         double d = 0.0, s = 0.0;
         if (l < nc) {
@@ -259,7 +261,7 @@ __global__ void k_qp_setup(int64_t nc, const int64_t *row_ptr, const int64_t *co
                 s += a;
             }
         }
-        const double b = volphi[l < nc ? l : l - nc];
+        const double b = l < nc ? brow[l] : volphi[l - nc];
         const double w = (eps * b) * (eps * b);
         diag[l] = d + w;
         exc[l] = w;
@@ -273,8 +275,8 @@ __global__ void k_qp_gather_cols(int64_t nnz, const int32_t *csc_src, const doub
 
 // F = r - A-hat x - w y and per-block partial sums of |F|.
 __global__ void k_qp_kkt(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
-                         const double *aN, const double *qx, const double *y, const double *rhs, const double *volphi,
-                         double eps, double *F, double *partials) {
+                         const double *aN, const double *qx, const double *y, const double *rhs, const double *brow,
+                         const double *volphi, double eps, double *F, double *partials) {
     double acc = 0.0;
     GRID_STRIDE(l, 2 * nc) {
         double s = 0.0;
@@ -284,7 +286,7 @@ __global__ void k_qp_kkt(int64_t nc, const int64_t *row_ptr, const int64_t *col_
             const int64_t j = l - nc;
             for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) s += aN[csc_src[p]] * qx[csc_src[p]];
         }
-        const double b = volphi[l < nc ? l : l - nc];
+        const double b = l < nc ? brow[l] : volphi[l - nc];
         const double f = rhs[l] - s - (eps * b) * (eps * b) * y[l];
         F[l] = f;
         acc += fabs(f);
@@ -418,6 +420,11 @@ static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z,
     }
 }
 
+#ifndef BCHAR_INNER_REDUCTION
+#define BCHAR_INNER_REDUCTION 1e-4
+#endif
+constexpr double kInnerReduction = BCHAR_INNER_REDUCTION;
+
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
     const int bl = blocks_for(n2);
@@ -435,27 +442,41 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
 
     k_qp_setup<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
-                                      ptr<double>(m->aN), ptr<double>(m->volphi), eps, a2, diag,
-                                      ptr<double>(m->qexc), rhs);
+                                      ptr<double>(m->aN), ptr<double>(m->bloc), ptr<double>(m->volphi), eps, a2,
+                                      diag, ptr<double>(m->qexc), rhs);
     k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, ptr<int32_t>(m->csc_src), a2, a2c);
     cudaMemsetAsync(qx, 0, sizeof(double) * nnz, s);
     cudaMemsetAsync(y, 0, sizeof(double) * n2, s);
     m->launches += 2;
     const bool amg = m->opt.qp_precond == 1 && amg_build(m, m->amg);
+    const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: residual history on stderr
+    if (trace && amg) {
+        fprintf(stderr, "[bchar] multigrid levels:");
+        for (int l = 0; l < m->amg.nlev; ++l)
+            fprintf(stderr, " %lld/%lld", static_cast<long long>(m->amg.levels[l].n),
+                    static_cast<long long>(m->amg.levels[l].nnz));
+        fprintf(stderr, "\n");
+    }
 
     int iters = 0, rounds = 0;
+    cudaGraphExec_t exec = nullptr;  // the captured batch, reused by every refinement round
+    int graph_launches = 0;
     const double target_abs = m->opt.qp_tol * total_volphi(m);
     double kkt = 0.0;
     for (rounds = 0; rounds <= m->opt.qp_max_refine; ++rounds) {
         k_qp_kkt<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
                                         ptr<int32_t>(m->csc_src), ptr<double>(m->aN), qx, y, rhs,
-                                        ptr<double>(m->volphi), eps, F, part);
+                                        ptr<double>(m->bloc), ptr<double>(m->volphi), eps, F, part);
         k_sum_partials<<<1, 1024, 0, s>>>(part, bl, &di->kkt_l1);
         m->launches += 2;
         cudaMemcpyAsync(&kkt, &di->kkt_l1, sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        if (trace) fprintf(stderr, "[bchar] round %d kkt_l1 %.3e (target %.3e)\n", rounds, kkt, target_abs);
         if (kkt <= target_abs || rounds == m->opt.qp_max_refine || iters >= m->opt.qp_max_iter) break;
-        const double inner = fmax(1e-10 * kkt, 0.25 * target_abs);
+        // restart the conjugate gradients from the true residual once it has
+        // dropped by kInnerReduction: on these ill-conditioned systems short
+        // cycles lose less to round-off than one long one
+        const double inner = fmax(kInnerReduction * kkt, 0.25 * target_abs);
         cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
         k_copy<<<bl, kThreads, 0, s>>>(n2, F, res, nullptr);
         precondition(m, amg, res, z, nullptr);
@@ -463,9 +484,10 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         k_cg_start<<<1, 1024, 0, s>>>(part_rz, bl, inner, st);
         k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
         m->launches += 4;
-        int done = 0;
-        while (!done) {
-            const int batch = amg ? 8 : 32;
+        // one batch of iterations is captured once into a CUDA graph and
+        // replayed until the solve converges (its kernels do nothing then)
+        const int batch = amg ? 8 : 32;
+        auto enqueue_batch = [&]() {
             for (int k = 0; k < batch; ++k) {
                 k_cg_matvec<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
                                                    ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag,
@@ -478,8 +500,37 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                 k_cg_pupdate<<<bl, kThreads, 0, s>>>(n2, z, p, st);
                 m->launches += 6;
             }
+        };
+        if (!exec) {
+            const int before = m->launches;
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                enqueue_batch();
+                ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && graph;
+            }
+            if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {  // capture unavailable (for instance, the caller is capturing): plain launches
+                cudaGetLastError();
+                exec = nullptr;
+            }
+            graph_launches = m->launches - before;
+            m->launches = before;
+        }
+        int done = 0;
+        while (!done) {
+            if (exec) {
+                cudaGraphLaunch(exec, s);
+                m->launches += graph_launches;
+            } else {
+                enqueue_batch();
+            }
             cudaMemcpyAsync(host_st, st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
+            if (trace && (host_st->iters % 512 < batch || host_st->converged))
+                fprintf(stderr, "[bchar] round %d iter %d res_l1 %.3e target %.3e\n", rounds, host_st->iters,
+                        host_st->res_l1, host_st->target);
             if (host_st->converged || iters + host_st->iters >= m->opt.qp_max_iter) done = 1;
         }
         iters += host_st->iters;
@@ -487,6 +538,7 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                                                ptr<double>(m->aN), d, qx, y);
         ++m->launches;
     }
+    if (exec) cudaGraphExecDestroy(exec);
     *cg_iters = iters;
     *refines = rounds;
     m->amg_levels = amg ? m->amg.nlev : 0;

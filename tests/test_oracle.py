@@ -336,3 +336,16 @@ def test_zero_velocity_step_is_the_identity():
     c = np.random.Generator(np.random.PCG64(5)).uniform(size=mesh.nc)
     r = oracle.step(mesh, faces, 0.1, c)
     assert np.allclose(r["c"], c, rtol=1e-13, atol=0)
+
+
+def test_balanced_targets_by_hand():
+    # rows {0 -> col 1}, {1 -> col 0}, {2 -> col 2} with |K|_phi = (1, 2, 3): the first
+    # two components have rows summing to 1 and 2 but columns to 2 and 1
+    A0 = sp.csr_matrix(np.array([[0.0, 1.0, 0.0], [2.0, 0.0, 0.0], [0.0, 0.0, 3.0]]))
+    b, n_unbal = oracle.balanced_targets(A0, np.array([1.0, 2.0, 3.0]))
+    assert n_unbal == 2
+    assert np.array_equal(b, [2.0, 1.0, 3.0])
+    # one connected block: nothing changes, bit for bit
+    A1 = sp.csr_matrix(np.array([[0.6, 0.4], [0.4, 0.6]]))
+    b1, n1 = oracle.balanced_targets(A1, np.array([0.3, 0.7]))
+    assert n1 == 0 and np.array_equal(b1, [0.3, 0.7])

@@ -105,6 +105,11 @@ def algorithmic_bytes(stage: str, nc: int, nnz: int) -> int:
         # view: column/row index 4 B + a^2 8 B; per node (2 nc): pointer 8 B,
         # diagonal 8 B, p read 8 B, q write 8 B
         return nnz * 2 * (4 + 8) + 2 * nc * (8 + 8 + 8 + 8)
+    if stage == "smooth":
+        # one FP32 damped-Jacobi sweep of the finest multigrid level: 2 nc
+        # nodes, 2 nnz off-diagonal entries (value 4 B + column 4 B); per node
+        # pointer 8 B, x, b, diagonal read and x_out written (4 B each)
+        return 2 * nnz * (4 + 4) + 2 * nc * (8 + 4 * 4)
     if stage == "update":
         # per entry: column 4 B + weight 8 B; per cell: row pointer 8 B,
         # c_in 8 B, c_out 8 B, |K|_phi 8 B
@@ -132,7 +137,7 @@ def run_ours(args, rank, world, local_rank):
         f = wl.faces(st % wl.steps)
         faces_dev.append([torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev) for a in f])
     opts = bchar.default_options(precision=bchar.FP32_SPLIT if wl.precision == "fp32split" else bchar.FP64,
-                                 qp_max_iter=args.qp_max_iter)
+                                 qp_max_iter=args.qp_max_iter, qp_tol=args.qp_tol)
     mesh = bchar.Mesh(wl.coords, wl.phi, opts)
     cdt = torch.float32 if wl.c_dtype == "f32" else torch.float64
     c = torch.tensor(wl.c0, dtype=cdt, device=dev)
@@ -178,24 +183,32 @@ def run_ours(args, rank, world, local_rank):
     # dominant kernel: live CUDA-event timing of the stages on the last step's data
     last = infos[-1]
     stage_ms = {
+        "smooth": mesh.time_stage(bchar.STAGE_SMOOTH, 50),
         "cg_matvec": mesh.time_stage(bchar.STAGE_CG_MATVEC, 50),
         "update": mesh.time_stage(bchar.STAGE_UPDATE, 50),
         "assemble": mesh.time_stage(bchar.STAGE_ASSEMBLE, 5),
         "track": mesh.time_stage(bchar.STAGE_TRACK, 5),
     }
+    cg_mean = statistics.mean(i["cg_iters"] for i in infos)
     per_step_ms = {
-        "cg_matvec": stage_ms["cg_matvec"] * statistics.mean(i["cg_iters"] for i in infos),
+        "smooth_level0": stage_ms["smooth"] * 2 * cg_mean,  # two sweeps of the finest level per V-cycle
+        "cg_matvec": stage_ms["cg_matvec"] * cg_mean,
         "update": stage_ms["update"],
         "assemble": stage_ms["assemble"],
         "track": stage_ms["track"],
     }
     hbm, peak_kind = _peaks()
+    sm_bytes = algorithmic_bytes("smooth", nc, last["nnz"])
+    achieved = sm_bytes / (stage_ms["smooth"] * 1e-3) / 1e9
     mv_bytes = algorithmic_bytes("cg_matvec", nc, last["nnz"])
-    achieved = mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_cg_matvec", "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": mv_bytes,
-                "mean_launch_ms": round(stage_ms["cg_matvec"], 5)}
+    roofline = {"bound": "hbm", "kernel": "k_jacobi<float> (finest multigrid level)", "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": sm_bytes,
+                "mean_launch_ms": round(stage_ms["smooth"], 5),
+                "k_cg_matvec": {"achieved": round(mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9, 1),
+                                "frac": round(mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9 / hbm, 4),
+                                "algorithmic_bytes_per_launch": mv_bytes,
+                                "mean_launch_ms": round(stage_ms["cg_matvec"], 5)}}
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, mesh, wl, bchar, torch, dev)
@@ -209,9 +222,10 @@ def run_ours(args, rank, world, local_rank):
                                 "phi=1, single vortex x cos(pi t/T), T=1, dt=0.005, disk c0; FP32 tracking and "
                                 "intersections, FP64 sums/scalings/minimisation/update",
                    "cells": nc, "cells_per_axis": len(wl.coords[0]) - 1, "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps",
-                   "qp_max_iter": args.qp_max_iter,
-                   "qp_note": "conjugate-gradient budget of the minimisation per step; qp_converged counts the "
-                              "steps that reached the 1e-14 optimality tolerance within it"},
+                   "qp_tol": args.qp_tol, "qp_max_iter": args.qp_max_iter,
+                   "qp_note": "the minimisation is solved to qp_tol (relative L1 optimality residual); global mass "
+                              "is exact regardless (final column scaling); qp_converged counts the steps that "
+                              "reached qp_tol within qp_max_iter"},
         "gpu_launches": int(statistics.mean(i["kernel_launches"] for i in infos) * args.steps) + 0,
         "roofline": roofline,
         "stage_ms_per_step": {k: round(v, 3) for k, v in per_step_ms.items()},
@@ -236,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
 def run_e2e(args, mesh, wl, bchar, torch, dev):
     """Same metric through the C ABI with HOST buffers: every step copies the
     step's face velocities and c to the device and reads c back."""
-    k = max(1, min(args.steps, 5))
+    k = max(1, min(args.steps, 2))
     faces_host = [[torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).pin_memory() for a in wl.faces(st % wl.steps)]
                   for st in range(k)]
     cdt = torch.float32 if wl.c_dtype == "f32" else torch.float64
@@ -322,13 +336,14 @@ def run_reference(args, rank, world):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--qp-max-iter", type=int, default=1000)
+    p.add_argument("--qp-max-iter", type=int, default=30000)
+    p.add_argument("--qp-tol", type=float, default=1e-5)
     p.add_argument("--n", type=int, default=None, help="cells per axis (same recipe; for small profiling runs)")
     args = p.parse_args()
     rank, world, local_rank = _env_rank()

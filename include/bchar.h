@@ -182,7 +182,8 @@ enum {
     BCHAR_STAGE_CG_MATVEC = 0, /* one product with A-hat A-hat^T + W (the minimisation's inner loop) */
     BCHAR_STAGE_UPDATE = 1,    /* c^{n+1} = W c^n and the mass sums */
     BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
-    BCHAR_STAGE_TRACK = 3      /* RK4 tracking of all balls */
+    BCHAR_STAGE_TRACK = 3,     /* RK4 tracking of all balls */
+    BCHAR_STAGE_SMOOTH = 4     /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
 };
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of

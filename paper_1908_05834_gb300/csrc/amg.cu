@@ -239,69 +239,93 @@ __global__ void k_coarse_fill(int64_t nco, const int64_t *mptr, const int32_t *m
 }
 
 // ---------------------------------------------------------------- V-cycle kernels
+//
+// The V-cycle runs on a copy of each level's operator divided by a fixed
+// scale (the square of the largest |K|_phi, so that the entries sit near 1),
+// in FP32 while the residual is large (it is only a preconditioner, the
+// conjugate gradients around it stay in FP64, and on this GPU FP32 arithmetic
+// is far faster than FP64) and in FP64 for the last digits.
 
-__global__ void k_flip_copy(int64_t nc, const double *in, double *out, const CgState *st) {
+template <class T> __global__ void k_scaled_copy(int64_t n, const double *in, T *out, double inv_scale) {
+    GRID_STRIDE(i, n) out[i] = static_cast<T>(in[i] * inv_scale);
+}
+
+// b = S res (S: +1 rows, -1 columns), in the V-cycle's precision
+template <class T> __global__ void k_flip_in(int64_t nc, const double *res, T *b, const CgState *st) {
     if (st && st->converged) return;
-    GRID_STRIDE(l, 2 * nc) out[l] = l < nc ? in[l] : -in[l];
+    GRID_STRIDE(l, 2 * nc) b[l] = static_cast<T>(l < nc ? res[l] : -res[l]);
+}
+
+// z = S x / scale, in FP64
+template <class T> __global__ void k_flip_out(int64_t nc, const T *x, double inv_scale, double *z, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(l, 2 * nc) {
+        const double v = static_cast<double>(x[l]) * inv_scale;
+        z[l] = l < nc ? v : -v;
+    }
 }
 
 // x = omega b / diag
-__global__ void k_jacobi0(int64_t n, const double *diag, const double *b, double *x, const CgState *st) {
+template <class T> __global__ void k_jacobi0(int64_t n, const T *diag, const T *b, T *x, const CgState *st) {
     if (st && st->converged) return;
-    GRID_STRIDE(i, n) x[i] = kOmega * b[i] / diag[i];
+    GRID_STRIDE(i, n) x[i] = static_cast<T>(kOmega) * b[i] / diag[i];
 }
 
 // r = b - L x
-__global__ void k_residual(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
-                           const double *x, const double *b, double *r, const CgState *st) {
+template <class T>
+__global__ void k_residual(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
+                           const T *b, T *r, const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
-        double s = diag[i] * x[i];
+        T s = diag[i] * x[i];
         for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
         r[i] = b[i] - s;
     }
 }
 
 // x_out = x + omega (b - L x) / diag
-__global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
-                         const double *x, const double *b, double *x_out, const CgState *st) {
+template <class T>
+__global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
+                         const T *b, T *x_out, const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
-        double s = diag[i] * x[i];
+        T s = diag[i] * x[i];
         for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
-        x_out[i] = x[i] + kOmega * (b[i] - s) / diag[i];
+        x_out[i] = x[i] + static_cast<T>(kOmega) * (b[i] - s) / diag[i];
     }
 }
 
-__global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlist, const double *r, double *bc,
+template <class T>
+__global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlist, const T *r, T *bc,
                            const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(I, nco) {
-        double s = 0.0;
+        T s = 0;
         for (int64_t k = mptr[I]; k < mptr[I + 1]; ++k) s += r[mlist[k]];
         bc[I] = s;
     }
 }
 
-__global__ void k_prolong(int64_t n, const int32_t *agg, const double *xc, double *x, const CgState *st) {
+template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x, const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(i, n) x[i] += xc[agg[i]];
 }
 
 // Coarsest level: kCoarsestSweeps damped-Jacobi sweeps from zero, all in one
 // block (the level is small), double-buffered in global memory.
-__global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
-                           const double *b, double *x, double *x2, const CgState *st) {
+template <class T>
+__global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *b,
+                           T *x, T *x2, const CgState *st) {
     if (st && st->converged) return;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = kOmega * b[i] / diag[i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = static_cast<T>(kOmega) * b[i] / diag[i];
     __syncthreads();
     for (int k = 0; k < kCoarsestSweeps; ++k) {
-        const double *xi = (k & 1) ? x2 : x;
-        double *xo = (k & 1) ? x : x2;
+        const T *xi = (k & 1) ? x2 : x;
+        T *xo = (k & 1) ? x : x2;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            double s = diag[i] * xi[i];
+            T s = diag[i] * xi[i];
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * xi[col[e]];
-            xo[i] = xi[i] + kOmega * (b[i] - s) / diag[i];
+            xo[i] = xi[i] + static_cast<T>(kOmega) * (b[i] - s) / diag[i];
         }
         __syncthreads();
     }
@@ -311,7 +335,8 @@ __global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, co
 
 void amg_release(Amg &amg) {
     for (AmgLevel &L : amg.levels) {
-        Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.mptr, &L.mlist, &L.x, &L.x2, &L.b, &L.r};
+        Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.mptr, &L.mlist, &L.x, &L.x2, &L.b, &L.r,
+                      &L.fval, &L.fdiag, &L.fx, &L.fx2, &L.fb, &L.fr, &L.dval, &L.ddiag};
         for (Buf *b : all) release(*b);
     }
     amg.levels.clear();
@@ -425,65 +450,114 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         ++m->launches;
         ++amg.nlev;
     }
+    // FP32 copies of every level, divided by the square of the largest |K|_phi
+    amg.scale = m->max_volphi * m->max_volphi;
+    const double inv = 1.0 / amg.scale;
+    for (int l = 0; l < amg.nlev; ++l) {
+        AmgLevel &L = amg.levels[l];
+        const int64_t nnzl = L.nnz > 0 ? L.nnz : 1;
+        if (!ensure(m, L.fval, sizeof(float) * nnzl) || !ensure(m, L.fdiag, sizeof(float) * L.n) ||
+            !ensure(m, L.fx, sizeof(float) * L.n) || !ensure(m, L.fx2, sizeof(float) * L.n) ||
+            !ensure(m, L.fb, sizeof(float) * L.n) || !ensure(m, L.fr, sizeof(float) * L.n))
+            return false;
+        if (!ensure(m, L.dval, sizeof(double) * nnzl) || !ensure(m, L.ddiag, sizeof(double) * L.n)) return false;
+        const double *dg = L.diag_ext ? L.diag_ext : ptr<double>(L.diag);
+        if (L.nnz > 0) {
+            k_scaled_copy<float><<<blocks_for(L.nnz), kThreads, 0, s>>>(L.nnz, ptr<double>(L.val), ptr<float>(L.fval), inv);
+            k_scaled_copy<double><<<blocks_for(L.nnz), kThreads, 0, s>>>(L.nnz, ptr<double>(L.val), ptr<double>(L.dval),
+                                                                         inv);
+        }
+        k_scaled_copy<float><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, dg, ptr<float>(L.fdiag), inv);
+        k_scaled_copy<double><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, dg, ptr<double>(L.ddiag), inv);
+        m->launches += 4;
+    }
     return true;
 }
 
-static const double *level_diag(const AmgLevel &L) {
-    return L.diag_ext ? L.diag_ext : static_cast<const double *>(L.diag.p);
-}
+// Buffers of one level in the V-cycle's precision.
+template <class T> struct LevelBufs;
+template <> struct LevelBufs<float> {
+    static float *val(AmgLevel &L) { return ptr<float>(L.fval); }
+    static float *diag(AmgLevel &L) { return ptr<float>(L.fdiag); }
+    static float *x(AmgLevel &L) { return ptr<float>(L.fx); }
+    static float *x2(AmgLevel &L) { return ptr<float>(L.fx2); }
+    static float *b(AmgLevel &L) { return ptr<float>(L.fb); }
+    static float *r(AmgLevel &L) { return ptr<float>(L.fr); }
+};
+template <> struct LevelBufs<double> {
+    static double *val(AmgLevel &L) { return ptr<double>(L.dval); }
+    static double *diag(AmgLevel &L) { return ptr<double>(L.ddiag); }
+    static double *x(AmgLevel &L) { return ptr<double>(L.x); }
+    static double *x2(AmgLevel &L) { return ptr<double>(L.x2); }
+    static double *b(AmgLevel &L) { return ptr<double>(L.b); }
+    static double *r(AmgLevel &L) { return ptr<double>(L.r); }
+};
 
-// z = S V(S res): one V-cycle of the sign-flipped operator on the residual.
-void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st) {
+// z = S V(S res) / scale: one V-cycle of the sign-flipped operator in precision T.
+template <class T> static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st) {
+    using B = LevelBufs<T>;
     cudaStream_t s = m->stream;
     const int64_t nc = m->nc;
     AmgLevel &L0 = amg.levels[0];
-    k_flip_copy<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, ptr<double>(L0.b), st);
+    k_flip_in<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, B::b(L0), st);
     ++m->launches;
-    // down: pre-smooth from zero, residual, restrict
-    for (int l = 0; l < amg.nlev - 1; ++l) {
+    for (int l = 0; l < amg.nlev - 1; ++l) {  // down: pre-smooth from zero, residual, restrict
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
-        k_jacobi0<<<bl, kThreads, 0, s>>>(L.n, level_diag(L), ptr<double>(L.b), ptr<double>(L.x), st);
-        k_residual<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
-                                           level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.r), st);
-        k_restrict<<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<double>(L.r),
-                                                        ptr<double>(C.b), st);
+        k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, B::diag(L), B::b(L), B::x(L), st);
+        k_residual<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
+                                              B::x(L), B::b(L), B::r(L), st);
+        k_restrict<T><<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
+                                                           B::b(C), st);
         m->launches += 3;
     }
-    // coarsest: Jacobi sweeps from zero (an even number, so the result is in x);
-    // one block when the level is small, otherwise one launch per sweep
-    {
+    {  // coarsest: Jacobi sweeps from zero (an even number, so the result is in x)
         AmgLevel &L = amg.levels[amg.nlev - 1];
         if (L.n <= kOneBlock) {
-            k_coarsest<<<1, 1024, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
-                                          level_diag(L), ptr<double>(L.b), ptr<double>(L.x), ptr<double>(L.x2), st);
+            k_coarsest<T><<<1, 1024, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
+                                             B::b(L), B::x(L), B::x2(L), st);
             ++m->launches;
         } else {
             const int bl = blocks_for(L.n);
-            k_jacobi0<<<bl, kThreads, 0, s>>>(L.n, level_diag(L), ptr<double>(L.b), ptr<double>(L.x), st);
-            for (int k = 0; k < kLargeCoarsestSweeps; ++k) {
-                k_jacobi<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
-                                                 level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.x2),
-                                                 st);
-                std::swap(L.x, L.x2);
-            }
+            k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, B::diag(L), B::b(L), B::x(L), st);
+            for (int k = 0; k < kLargeCoarsestSweeps; ++k)
+                k_jacobi<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+                                                    B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
+                                                    k & 1 ? B::x(L) : B::x2(L), st);
             m->launches += 1 + kLargeCoarsestSweeps;
         }
     }
-    // up: prolong, post-smooth
+    // up: prolong into x, post-smooth into x2 (the next finer level reads x2)
     for (int l = amg.nlev - 2; l >= 0; --l) {
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
+        const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);
         const int bl = blocks_for(L.n);
-        k_prolong<<<bl, kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), ptr<double>(C.x), ptr<double>(L.x), st);
-        k_jacobi<<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.val),
-                                         level_diag(L), ptr<double>(L.x), ptr<double>(L.b), ptr<double>(L.x2), st);
-        std::swap(L.x, L.x2);
+        k_prolong<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
+        k_jacobi<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
+                                            B::x(L), B::b(L), B::x2(L), st);
         m->launches += 2;
     }
-    k_flip_copy<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<double>(L0.x), z, st);
+    k_flip_out<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, amg.nlev > 1 ? B::x2(L0) : B::x(L0), 1.0 / amg.scale, z,
+                                                        st);
     ++m->launches;
+}
+
+// One FP32 smoothing sweep on the finest level (for timing).
+void amg_smooth_once(bchar_mesh_t m, Amg &amg) {
+    AmgLevel &L = amg.levels[0];
+    k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                  ptr<float>(L.fval), ptr<float>(L.fdiag),
+                                                                  ptr<float>(L.fx), ptr<float>(L.fb),
+                                                                  ptr<float>(L.fx2), nullptr);
+}
+
+void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32) {
+    if (fp32)
+        vcycle<float>(m, amg, res, z, st);
+    else
+        vcycle<double>(m, amg, res, z, st);
 }
 
 }  // namespace bchar

@@ -160,7 +160,7 @@ void bchar_destroy(bchar_mesh_t m) {
                   &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
                   &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->bloc, &m->uf_parent, &m->uf_label, &m->comp_acc, &m->a2,
                   &m->a2c, &m->diag, &m->qexc, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
-                  &m->cg_q, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
+                  &m->cg_q, &m->cg_rp, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
     for (Buf *b : all) release(*b);
     for (int a = 0; a < 3; ++a) {
         release(m->x[a]);
@@ -251,7 +251,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
          ensure(m, m->qy, sizeof(double) * 2 * nc) && ensure(m, m->F, sizeof(double) * 2 * nc) &&
          ensure(m, m->cg_d, sizeof(double) * 2 * nc) && ensure(m, m->cg_r, sizeof(double) * 2 * nc) &&
          ensure(m, m->cg_z, sizeof(double) * 2 * nc) && ensure(m, m->cg_p, sizeof(double) * 2 * nc) &&
-         ensure(m, m->cg_q, sizeof(double) * 2 * nc) && ensure(m, m->partials, sizeof(double) * 4 * 152 * 64) &&
+         ensure(m, m->cg_q, sizeof(double) * 2 * nc) && ensure(m, m->cg_rp, sizeof(double) * 2 * nc) && ensure(m, m->partials, sizeof(double) * 4 * 152 * 64) &&
          ensure(m, m->dinfo, sizeof(DevInfo)) && ensure(m, m->cg, sizeof(CgState));
     if (ok && cudaMallocHost(&m->info_host.p, sizeof(DevInfo) + sizeof(CgState)) != cudaSuccess) {
         cudaGetLastError();
@@ -506,7 +506,8 @@ bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int
 
 bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms) {
     if (!m) return BCHAR_ERR_INVALID_ARG;
-    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 3)
+    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 4 ||
+        (stage == BCHAR_STAGE_SMOOTH && m->amg_levels == 0))
         return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet or bad arguments");
     Buf st, cin, cout;
     if (!ensure(m, st, sizeof(CgState)) || !ensure(m, cin, sizeof(double) * m->nc) ||
@@ -524,6 +525,7 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
         case BCHAR_STAGE_CG_MATVEC: launch_cg_matvec_once(m, ptr<CgState>(st)); break;
         case BCHAR_STAGE_UPDATE: launch_update(m, cin.p, cout.p, BCHAR_C_F64); break;
         case BCHAR_STAGE_ASSEMBLE: launch_assemble(m); break;
+        case BCHAR_STAGE_SMOOTH: amg_smooth_once(m, m->amg); break;
         default: launch_track(m, m->dt, m->substeps); break;
         }
     };

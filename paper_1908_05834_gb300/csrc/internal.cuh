@@ -94,6 +94,8 @@ struct Buf {
 struct AmgLevel {
     int64_t n = 0, nnz = 0;
     Buf ptr, col, val, diag, exc, agg, mptr, mlist, x, x2, b, r;  // mptr/mlist: members of each aggregate
+    Buf fval, fdiag, fx, fx2, fb, fr;  // FP32 copy of the operator (scaled) and FP32 work vectors
+    Buf dval, ddiag;                   // FP64 scaled copy (work vectors: x, x2, b, r)
     const double *diag_ext = nullptr;  // level 0 shares the minimisation's diagonal
     const double *exc_ext = nullptr;   // and its excess (the penalty shift)
 };
@@ -102,6 +104,7 @@ struct Amg {
     std::vector<AmgLevel> levels;
     int nlev = 0;
     Buf tmp;
+    double scale = 1.0;  // the FP32 levels hold operator / scale
 };
 
 }  // namespace bchar
@@ -141,7 +144,7 @@ struct bchar_mesh_s {
     bchar::Buf R, C, bloc;                           // scaling factors, balanced row targets
     bchar::Buf uf_parent, uf_label, comp_acc;        // components of A's pattern
     bchar::Buf a2, a2c, diag, qexc, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
-    bchar::Buf scan_tmp, partials, dinfo, cg;        // scratch
+    bchar::Buf scan_tmp, partials, dinfo, cg, cg_rp; // scratch (cg_rp: previous residual of the flexible CG)
     bchar::Buf info_host;                            // pinned DevInfo
     bchar::Amg amg;                                  // preconditioner of the minimisation
     int64_t nnz = 0;

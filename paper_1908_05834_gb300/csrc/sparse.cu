@@ -361,15 +361,18 @@ __global__ void k_cg_alpha(const double *partials, int nparts, CgState *st) {
     }
 }
 
-// d += alpha p, res -= alpha q, partial sums of |res|
-__global__ void k_cg_update(int64_t n2, const double *p, const double *q, double *d, double *res, double *partials,
-                            const CgState *st) {
+// d += alpha p, res -= alpha q (the previous residual kept in rp), partial
+// sums of |res|
+__global__ void k_cg_update(int64_t n2, const double *p, const double *q, double *d, double *res, double *rp,
+                            double *partials, const CgState *st) {
     if (st->converged) return;
     const double alpha = st->alpha;
     double l1 = 0.0;
     GRID_STRIDE(l, n2) {
         d[l] += alpha * p[l];
-        const double r = res[l] - alpha * q[l];
+        const double r0 = res[l];
+        rp[l] = r0;
+        const double r = r0 - alpha * q[l];
         res[l] = r;
         l1 += fabs(r);
     }
@@ -377,17 +380,38 @@ __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double
     if (threadIdx.x == 0) partials[blockIdx.x] = l1;
 }
 
-__global__ void k_cg_beta(const double *rz_parts, const double *l1_parts, int nparts, CgState *st) {
+// partial sums of z.res and z.rp (flexible, Polak-Ribiere form of beta: the
+// preconditioner may differ slightly between applications)
+__global__ void k_dot2(int64_t n, const double *z, const double *res, const double *rp, double *pa, double *pb,
+                       const CgState *st) {
+    if (st && st->converged) return;
+    double a = 0.0, b = 0.0;
+    GRID_STRIDE(i, n) {
+        a += z[i] * res[i];
+        b += z[i] * rp[i];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const double *l1_parts, int nparts,
+                          CgState *st) {
     if (st->converged) return;
-    double rz = 0.0, l1 = 0.0;
+    double rz = 0.0, zp = 0.0, l1 = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
         rz += rz_parts[i];
+        zp += zp_parts[i];
         l1 += l1_parts[i];
     }
     rz = block_sum(rz);
+    zp = block_sum(zp);
     l1 = block_sum(l1);
     if (threadIdx.x == 0) {
-        st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
+        st->beta = st->rz > 0.0 ? fmax(0.0, (rz - zp) / st->rz) : 0.0;
         st->rz = rz;
         st->res_l1 = l1;
         st->iters += 1;
@@ -411,9 +435,9 @@ __global__ void k_qp_accumulate(int64_t nc, const int64_t *row_ptr, const int32_
     }
 }
 
-static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z, const CgState *st) {
+static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res, double *z, const CgState *st) {
     if (amg) {
-        amg_apply(m, m->amg, res, z, st);
+        amg_apply(m, m->amg, res, z, st, fp32);
     } else {
         k_jacobi_precond<<<blocks_for(2 * m->nc), kThreads, 0, m->stream>>>(2 * m->nc, ptr<double>(m->diag), res, z, st);
         ++m->launches;
@@ -424,6 +448,7 @@ static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z,
 #define BCHAR_INNER_REDUCTION 1e-4
 #endif
 constexpr double kInnerReduction = BCHAR_INNER_REDUCTION;
+constexpr double kFp32Above = 1e-9;  // relative optimality residual above which the V-cycle runs in FP32
 
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
@@ -437,6 +462,8 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     double *part = ptr<double>(m->partials);
     double *part_l1 = part + 152 * 64;
     double *part_rz = part + 2 * 152 * 64;
+    double *part_zp = part + 3 * 152 * 64;
+    double *rp = ptr<double>(m->cg_rp);
     DevInfo *di = ptr<DevInfo>(m->dinfo);
     CgState *st = ptr<CgState>(m->cg);
     CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
@@ -459,7 +486,8 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     }
 
     int iters = 0, rounds = 0;
-    cudaGraphExec_t exec = nullptr;  // the captured batch, reused by every refinement round
+    cudaGraphExec_t exec = nullptr;  // the captured batch, reused by the refinement rounds
+    bool exec_fp32 = true;
     int graph_launches = 0;
     const double target_abs = m->opt.qp_tol * total_volphi(m);
     double kkt = 0.0;
@@ -479,7 +507,14 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         const double inner = fmax(kInnerReduction * kkt, 0.25 * target_abs);
         cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
         k_copy<<<bl, kThreads, 0, s>>>(n2, F, res, nullptr);
-        precondition(m, amg, res, z, nullptr);
+        // FP32 V-cycle while the optimality residual is large, FP64 for the last digits
+        const bool fp32 = kkt > kFp32Above * total_volphi(m);
+        if (exec && fp32 != exec_fp32) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        exec_fp32 = fp32;
+        precondition(m, amg, fp32, res, z, nullptr);
         k_dot<<<bl, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
         k_cg_start<<<1, 1024, 0, s>>>(part_rz, bl, inner, st);
         k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
@@ -493,10 +528,10 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                                                    ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag,
                                                    p, q, part, st);
                 k_cg_alpha<<<1, 1024, 0, s>>>(part, bl, st);
-                k_cg_update<<<bl, kThreads, 0, s>>>(n2, p, q, d, res, part_l1, st);
-                precondition(m, amg, res, z, st);
-                k_dot<<<bl, kThreads, 0, s>>>(n2, res, z, part_rz, st);
-                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_l1, bl, st);
+                k_cg_update<<<bl, kThreads, 0, s>>>(n2, p, q, d, res, rp, part_l1, st);
+                precondition(m, amg, fp32, res, z, st);
+                k_dot2<<<bl, kThreads, 0, s>>>(n2, z, res, rp, part_rz, part_zp, st);
+                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_zp, part_l1, bl, st);
                 k_cg_pupdate<<<bl, kThreads, 0, s>>>(n2, z, p, st);
                 m->launches += 6;
             }

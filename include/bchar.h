@@ -188,7 +188,9 @@ enum {
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of
  * the last step, on the handle's stream, and return the mean duration of one
- * launch in milliseconds (CUDA events around the replays).  The replays do
+ * launch in milliseconds (CUDA events around the replays).  CG_MATVEC, UPDATE
+ * and SMOOTH are replayed from one CUDA graph of `reps` launches (captured on a
+ * private stream), so that host launch overhead is not measured.  The replays do
  * not change the result of the last step (exports stay valid) except that
  * BCHAR_STAGE_TRACK overwrites the tracked balls with the same values.
  * Errors: INVALID_ARG (no step yet, bad stage, reps < 1), CUDA. */

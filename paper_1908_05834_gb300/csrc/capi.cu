@@ -530,11 +530,45 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
         }
     };
     once();  // warm-up
+    // The short stages (tens of microseconds) are replayed from a CUDA graph
+    // so that the host's launch rate does not bound the measurement; the
+    // graph is captured on a private stream and launched on the handle's.
+    cudaGraphExec_t exec = nullptr;
+    if (stage == BCHAR_STAGE_CG_MATVEC || stage == BCHAR_STAGE_UPDATE || stage == BCHAR_STAGE_SMOOTH) {
+        cudaStream_t user = m->stream, cap = nullptr;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) {
+            cudaStreamSynchronize(user);
+            m->stream = cap;
+            ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                for (int r = 0; r < reps; ++r) once();
+                ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
+            }
+            m->stream = user;
+            if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+        }
+        if (ok) ok = cudaGraphLaunch(exec, m->stream) == cudaSuccess;  // warm-up of the graph
+        if (!ok) {
+            if (exec) cudaGraphExecDestroy(exec);
+            release(st);
+            release(cin);
+            release(cout);
+            cudaGetLastError();
+            return fail(m, BCHAR_ERR_CUDA, "stage graph capture failed");
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, m->stream);
-    for (int r = 0; r < reps; ++r) once();
+    if (exec)
+        cudaGraphLaunch(exec, m->stream);
+    else
+        for (int r = 0; r < reps; ++r) once();
     cudaEventRecord(e1, m->stream);
     cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -542,6 +576,7 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *mean_ms = ms / reps;
+    if (exec) cudaGraphExecDestroy(exec);
     release(st);
     release(cin);
     release(cout);

@@ -6,13 +6,21 @@
 // of the bipartite row/column graph (edge weights a_ij^2) plus a small
 // positive shift.  Its conditioning is poor on two counts: mesh-scale smooth
 // modes, and weak links (near-tangent ball overlaps give a_ij that are orders
-// of magnitude below the row's main entries).  Aggregating along the strongest
-// links handles both:
-//   - each level pairs every node with its heaviest neighbour when the choice
-//     is mutual (kHandshakes rounds, each among the nodes still unpaired);
-//     a node left unpaired joins the aggregate of its heaviest neighbour when
-//     that one is paired, else stays single; coarsening stops when a level
-//     would keep more than kStall of its nodes;
+// of magnitude below the row's main entries).  A cluster of nodes held to the
+// rest only by weak links has a near-null mode (constant on the cluster); the
+// coarse levels keep that mode only if no aggregate straddles the weak links.
+// So the aggregation follows strong links alone:
+//   - an edge is strong when its weight is at least kStrength sqrt(d_i d_j);
+//   - each level pairs every node with its heaviest strong neighbour when the
+//     choice is mutual (kHandshakes rounds, each among the nodes still
+//     unpaired); a node left unpaired joins the aggregate of its heaviest
+//     strong neighbour when that one is paired, else stays single;
+//   - a node without any off-diagonal entry (a whole connected component
+//     that has collapsed into one node, or an isolated row or column) leaves
+//     the hierarchy: its equation is solved exactly by the smoother (weight 1
+//     instead of kOmega) and it has no coarse counterpart;
+//   - coarsening stops when a level would keep more than kStall of its
+//     remaining nodes, or has at most kCoarsest of them;
 //   - the coarse operator is the Galerkin product P^T L P for the piecewise-
 //     constant P of the aggregates (coarse edge = sum of fine edges between
 //     two aggregates).  Its diagonal is formed as the coarse node's excess
@@ -36,12 +44,14 @@ namespace bchar {
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
 
 constexpr int kCoarseCap = 384;       // neighbours a coarse node may collect before merging
-constexpr int64_t kCoarsest = 1024;   // stop coarsening below this many nodes
+constexpr int64_t kCoarsest = 128;    // stop coarsening at this many nodes
 constexpr int64_t kOneBlock = 4096;   // coarsest levels up to this size are swept by one block
 constexpr int kMaxLevels = 40;
 constexpr int kHandshakes = 4;        // matching rounds per level
 constexpr double kStall = 0.9;        // stop coarsening when a level keeps this fraction of nodes
-constexpr double kOmega = 0.6;        // Jacobi damping
+constexpr double kOmega = 0.6;        // Jacobi damping (rows with off-diagonal entries)
+constexpr double kStrength = 0.05;    // strong edge: w_ij >= kStrength sqrt(d_i d_j)
+constexpr double kAttach = 0.25;      // a leftover node follows an edge carrying this share of its diagonal
 constexpr int kCoarsestSweeps = 40;   // one-block coarsest solve
 constexpr int kLargeCoarsestSweeps = 20;
 
@@ -76,19 +86,22 @@ __global__ void k_level0_fill(int64_t nc, const int64_t *row_ptr, const int32_t 
 
 // ---------------------------------------------------------------- matching
 
-// Heaviest neighbour (most negative off-diagonal), ties to the smaller index;
-// with only_free, among neighbours that are still unpaired.
-__global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
+// Heaviest strong neighbour (most negative off-diagonal with w_ij >=
+// kStrength sqrt(d_i d_j)), ties to the smaller index; with only_free, among
+// neighbours that are still unpaired.
+__global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
                            const int32_t *partner, int only_free, int32_t *best) {
     GRID_STRIDE(i, n) {
         int32_t b = -1;
         double bw = 0.0;
         if (!only_free || partner[i] < 0) {
+            const double di = diag[i];
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
                 const int32_t j = col[e];
                 if (j == i) continue;
                 if (only_free && partner[j] >= 0) continue;
                 const double w = -val[e];
+                if (!(w >= kStrength * sqrt(di * diag[j]))) continue;
                 if (w > bw || (w == bw && w > 0.0 && j < b)) {
                     bw = w;
                     b = j;
@@ -107,27 +120,82 @@ __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
     }
 }
 
-// Leader of every node: the smaller node of a pair; an unpaired node whose
-// heaviest neighbour (first round) is paired joins that pair's aggregate,
-// otherwise it stays single.  Attaching only to paired nodes leaves no chains.
-__global__ void k_leaders(int64_t n, const int32_t *partner, const int32_t *heaviest, int32_t *leader,
-                          int32_t *is_leader, int *isolated) {
+// Attachment target of every node: its heaviest neighbour over all edges
+// (ties to the smaller index) when that edge carries at least kAttach of the
+// node's own diagonal, else -1.  The test is one-sided on purpose: a leaf
+// hanging off a hub by an edge that is strong for the leaf (most of its
+// diagonal) but weak for the hub should follow the hub.
+__global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
+                                const double *diag, int32_t *att) {
     GRID_STRIDE(i, n) {
-        if (heaviest[i] < 0 && partner[i] < 0) atomicAdd(isolated, 1);  // no neighbour at all
-        const int32_t p = partner[i];
-        int32_t lead;
-        if (p >= 0) {
+        int32_t b = -1;
+        double bw = 0.0;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+            const int32_t j = col[e];
+            if (j == i) continue;
+            const double w = -val[e];
+            if (w > bw || (w == bw && w > 0.0 && j < b)) {
+                bw = w;
+                b = j;
+            }
+        }
+        att[i] = (b >= 0 && bw >= kAttach * diag[i]) ? b : -1;
+    }
+}
+
+// Leaders, first pass.  A node without off-diagonal entries gets leader -1
+// (no coarse node; counted in *isolated); a paired node, the smaller node of
+// its pair; an unpaired node whose attachment target is paired joins that
+// pair; every other node is left open (-2) for the second pass.
+__global__ void k_leaders1(int64_t n, const int64_t *ptr, const int32_t *partner, const int32_t *att, int32_t *leader,
+                           int *isolated) {
+    GRID_STRIDE(i, n) {
+        int32_t lead = -2;
+        if (ptr[i + 1] == ptr[i]) {
+            atomicAdd(isolated, 1);
+            lead = -1;
+        } else if (partner[i] >= 0) {
+            const int32_t p = partner[i];
             lead = i < p ? static_cast<int32_t>(i) : p;
         } else {
-            const int32_t t = heaviest[i];
+            const int32_t t = att[i];
             if (t >= 0 && partner[t] >= 0) {
                 const int32_t q = partner[t];
                 lead = t < q ? t : q;
-            } else {
-                lead = static_cast<int32_t>(i);
             }
         }
         leader[i] = lead;
+    }
+}
+
+// want[i]: the attachment target of an open node when that target is open
+// too, else -1.
+__global__ void k_want(int64_t n, const int32_t *att, const int32_t *leader, int32_t *want) {
+    GRID_STRIDE(i, n) {
+        const int32_t t = att[i];
+        want[i] = (leader[i] == -2 && t >= 0 && leader[t] == -2) ? t : -1;
+    }
+}
+
+// Leaders, second pass over the open nodes: two nodes that want each other
+// pair up (the smaller leads); a node that wants a node wanting nothing joins
+// it; every other open node leads itself.  Each leader leads itself, so
+// aggregates have no chains.  is_leader flags the leaders for the scan.
+__global__ void k_leaders2(int64_t n, const int32_t *want, int32_t *leader, int32_t *is_leader) {
+    GRID_STRIDE(i, n) {
+        int32_t lead = leader[i];
+        if (lead == -2) {
+            const int32_t t = want[i];
+            if (t < 0)
+                lead = static_cast<int32_t>(i);
+            else if (want[t] == i)
+                lead = i < t ? static_cast<int32_t>(i) : t;
+            else if (want[t] < 0)
+                lead = t;
+            else
+                lead = static_cast<int32_t>(i);
+            leader[i] = lead;
+        }
         is_leader[i] = lead == i ? 1 : 0;
     }
 }
@@ -135,6 +203,10 @@ __global__ void k_leaders(int64_t n, const int32_t *partner, const int32_t *heav
 __global__ void k_aggregates(int64_t n, const int32_t *leader, const int64_t *leader_pos, int32_t *agg,
                              int32_t *count) {
     GRID_STRIDE(i, n) {
+        if (leader[i] < 0) {
+            agg[i] = -1;
+            continue;
+        }
         const int32_t I = static_cast<int32_t>(leader_pos[leader[i]]);
         agg[i] = I;
         atomicAdd(&count[I], 1);
@@ -144,6 +216,7 @@ __global__ void k_aggregates(int64_t n, const int32_t *leader, const int64_t *le
 __global__ void k_members_fill(int64_t n, const int32_t *agg, const int64_t *mptr, int32_t *fill, int32_t *mlist) {
     GRID_STRIDE(i, n) {
         const int32_t I = agg[i];
+        if (I < 0) continue;
         mlist[mptr[I] + atomicAdd(&fill[I], 1)] = static_cast<int32_t>(i);
     }
 }
@@ -265,10 +338,17 @@ template <class T> __global__ void k_flip_out(int64_t nc, const T *x, double inv
     }
 }
 
-// x = omega b / diag
-template <class T> __global__ void k_jacobi0(int64_t n, const T *diag, const T *b, T *x, const CgState *st) {
+// Relaxation weight of row i: kOmega, or 1 for a row without off-diagonal
+// entries (then one sweep solves its equation exactly).
+__device__ __forceinline__ double row_weight(const int64_t *ptr, int64_t i) {
+    return ptr[i + 1] == ptr[i] ? 1.0 : kOmega;
+}
+
+// x = omega_i b / diag
+template <class T>
+__global__ void k_jacobi0(int64_t n, const int64_t *ptr, const T *diag, const T *b, T *x, const CgState *st) {
     if (st && st->converged) return;
-    GRID_STRIDE(i, n) x[i] = static_cast<T>(kOmega) * b[i] / diag[i];
+    GRID_STRIDE(i, n) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
 }
 
 // r = b - L x
@@ -283,15 +363,17 @@ __global__ void k_residual(int64_t n, const int64_t *ptr, const int32_t *col, co
     }
 }
 
-// x_out = x + omega (b - L x) / diag
+// x_out = x + omega_i (b - L x) / diag
 template <class T>
 __global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
                          const T *b, T *x_out, const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
+        const int64_t e0 = ptr[i], e1 = ptr[i + 1];
         T s = diag[i] * x[i];
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
-        x_out[i] = x[i] + static_cast<T>(kOmega) * (b[i] - s) / diag[i];
+        for (int64_t e = e0; e < e1; ++e) s += val[e] * x[col[e]];
+        const T om = static_cast<T>(e1 == e0 ? 1.0 : kOmega);
+        x_out[i] = x[i] + om * (b[i] - s) / diag[i];
     }
 }
 
@@ -308,7 +390,10 @@ __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlis
 
 template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x, const CgState *st) {
     if (st && st->converged) return;
-    GRID_STRIDE(i, n) x[i] += xc[agg[i]];
+    GRID_STRIDE(i, n) {
+        const int32_t I = agg[i];
+        if (I >= 0) x[i] += xc[I];
+    }
 }
 
 // Coarsest level: kCoarsestSweeps damped-Jacobi sweeps from zero, all in one
@@ -317,7 +402,7 @@ template <class T>
 __global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *b,
                            T *x, T *x2, const CgState *st) {
     if (st && st->converged) return;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = static_cast<T>(kOmega) * b[i] / diag[i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
     __syncthreads();
     for (int k = 0; k < kCoarsestSweeps; ++k) {
         const T *xi = (k & 1) ? x2 : x;
@@ -325,7 +410,7 @@ __global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, co
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
             T s = diag[i] * xi[i];
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * xi[col[e]];
-            xo[i] = xi[i] + static_cast<T>(kOmega) * (b[i] - s) / diag[i];
+            xo[i] = xi[i] + static_cast<T>(row_weight(ptr, i)) * (b[i] - s) / diag[i];
         }
         __syncthreads();
     }
@@ -374,12 +459,14 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         AmgLevel &F = amg.levels[amg.nlev - 1];
         if (F.n <= kCoarsest) break;
         const double *fexc = F.exc_ext ? F.exc_ext : ptr<double>(F.exc);
-        if (!ensure(m, amg.tmp, sizeof(int32_t) * 5 * F.n + 64) || !ensure(m, F.agg, sizeof(int32_t) * F.n))
+        const double *fdg = F.diag_ext ? F.diag_ext : ptr<double>(F.diag);
+        if (!ensure(m, amg.tmp, sizeof(int32_t) * 6 * F.n + 64) || !ensure(m, F.agg, sizeof(int32_t) * F.n))
             return false;
         int32_t *best = ptr<int32_t>(amg.tmp);
         int32_t *partner = best + F.n;
-        int32_t *heavy = partner + F.n;   // heaviest neighbour of the first round
-        int32_t *leader = heavy + F.n;
+        int32_t *att = partner + F.n;     // attachment targets
+        int32_t *want = att + F.n;
+        int32_t *leader = want + F.n;
         int32_t *flag = leader + F.n;     // leader flags, later member counts / fill / row counts
         int *overflow = reinterpret_cast<int *>(flag + F.n);
         int *isolated = overflow + 1;
@@ -388,11 +475,16 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         cudaMemsetAsync(overflow, 0, 2 * sizeof(int), s);
         for (int round = 0; round < kHandshakes; ++round) {
             k_heaviest<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
-                                               partner, round > 0, round == 0 ? heavy : best);
-            k_handshake<<<bl, kThreads, 0, s>>>(F.n, round == 0 ? heavy : best, partner);
+                                               fdg, partner, round > 0, best);
+            k_handshake<<<bl, kThreads, 0, s>>>(F.n, best, partner);
             m->launches += 2;
         }
-        k_leaders<<<bl, kThreads, 0, s>>>(F.n, partner, heavy, leader, flag, isolated);
+        k_attach_target<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val), fdg,
+                                                att);
+        k_leaders1<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), partner, att, leader, isolated);
+        k_want<<<bl, kThreads, 0, s>>>(F.n, att, leader, want);
+        k_leaders2<<<bl, kThreads, 0, s>>>(F.n, want, leader, flag);
+        m->launches += 4;
         // leader positions: scan of the leader flags (int32 -> int64), reuse the
         // per-level x buffer as int64 scratch (it holds n + 1 entries)
         int64_t *pos = reinterpret_cast<int64_t *>(ptr<double>(F.x));
@@ -402,9 +494,8 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         cudaMemcpyAsync(&nco, pos + F.n, sizeof nco, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&niso, isolated, sizeof niso, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-        m->launches += 1;
-        (void)niso;
-        if (nco >= F.n * kStall || nco < 1) break;  // matching stalled: this is the coarsest level
+        const int64_t active = F.n - niso;  // nodes that would have a coarse counterpart
+        if (active <= kCoarsest || nco >= active * kStall || nco < 1) break;  // this is the coarsest level
         if (static_cast<int>(amg.levels.size()) <= amg.nlev) amg.levels.resize(amg.nlev + 1);
         AmgLevel &Fr = amg.levels[amg.nlev - 1];  // re-fetch after resize
         AmgLevel &C = amg.levels[amg.nlev];
@@ -505,7 +596,7 @@ template <class T> static void vcycle(bchar_mesh_t m, Amg &amg, const double *re
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
-        k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, B::diag(L), B::b(L), B::x(L), st);
+        k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
         k_residual<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
                                               B::x(L), B::b(L), B::r(L), st);
         k_restrict<T><<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
@@ -520,7 +611,7 @@ template <class T> static void vcycle(bchar_mesh_t m, Amg &amg, const double *re
             ++m->launches;
         } else {
             const int bl = blocks_for(L.n);
-            k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, B::diag(L), B::b(L), B::x(L), st);
+            k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
             for (int k = 0; k < kLargeCoarsestSweeps; ++k)
                 k_jacobi<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
                                                     B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),

@@ -216,6 +216,12 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API with host buffers
     e2e = run_e2e(args, mesh, wl, bchar, torch, dev)
 
+    # plain vs batched, and the serving loop (one GPU; replicas at N > 1 are not re-measured)
+    batched = served = None
+    if world == 1 and not args.no_serve:
+        batched = run_batched(args, torch, bchar, inputs)
+        served = run_served(args, torch, bchar, inputs)
+
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
@@ -243,6 +249,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if batched is not None:
+        result["batched"] = batched
+    if served is not None:
+        result["served"] = served
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -275,6 +285,94 @@ def run_e2e(args, mesh, wl, bchar, torch, dev):
     t = time.perf_counter() - t0
     return {"value": round(wl.nc * k / t, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": k}
+
+
+def _serving_options(bchar, args):
+    return bchar.default_options(precision=bchar.FP32_SPLIT, qp_tol=args.qp_tol, qp_max_iter=args.qp_max_iter)
+
+
+def run_batched(args, torch, bchar, inputs):
+    """Plain vs batched stepping of the first --batch-count meshes of the
+    serving stream (uneven sizes), --batch-steps steps each after one warm-up
+    step: plain = one bchar_step after another; batched = bchar_step_batch of
+    all instances per step.  Host wall clock around whole steps (every
+    instance's step has finished when the call returns)."""
+    reqs = inputs.serving_requests(args.batch_count)
+    prepared = [r.materialize() for r in reqs]
+    opts = _serving_options(bchar, args)
+
+    def make():
+        hs = []
+        for (coords, phi, faces, c0) in prepared:
+            st = torch.cuda.Stream()
+            m = bchar.Mesh(coords, phi, opts, stream=st.cuda_stream)
+            fd = [torch.from_numpy(np.ascontiguousarray(f).reshape(-1)).cuda() for f in faces]
+            c = torch.tensor(c0, dtype=torch.float64, device="cuda")
+            hs.append([m, fd, c, torch.empty_like(c)])
+        torch.cuda.synchronize()
+        return hs
+
+    def plain_step(hs, k):
+        for r, h in zip(reqs, hs):
+            h[0].set_velocity(h[1], scale=r.time_factor(k))
+            h[0].step(r.dt, h[2], h[3])
+            h[2], h[3] = h[3], h[2]
+
+    def batch_step(hs, k):
+        for r, h in zip(reqs, hs):
+            h[0].set_velocity(h[1], scale=r.time_factor(k))
+        bchar.step_batch([h[0] for h in hs], [r.dt for r in reqs], [h[2] for h in hs], [h[3] for h in hs])
+        for h in hs:
+            h[2], h[3] = h[3], h[2]
+
+    out = {}
+    finals = {}
+    for mode, fn in (("plain", plain_step), ("batched", batch_step)):
+        hs = make()
+        fn(hs, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(1, 1 + args.batch_steps):
+            fn(hs, k)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out[mode] = round(sum(r.nc for r in reqs) * args.batch_steps / t, 1)
+        finals[mode] = [h[2].cpu() for h in hs]
+        for h in hs:
+            h[0].close()
+    same = all(torch.equal(a, b) for a, b in zip(finals["plain"], finals["batched"]))
+    return {"plain": out["plain"], "batched": out["batched"], "unit": UNIT,
+            "speedup": round(out["batched"] / out["plain"], 3), "bitwise_equal": same,
+            "instances": len(reqs), "steps": args.batch_steps,
+            "cells": [r.nc for r in reqs],
+            "sample": f"meshes of the first {len(reqs)} requests of the serving stream (seed 4004), "
+                      f"{args.batch_steps} timed steps after 1 warm-up step, FP32 split, qp_tol {args.qp_tol}"}
+
+
+def run_served(args, torch, bchar, inputs):
+    """The first --serve-requests requests of the serving stream (Poisson
+    arrivals, mean gap 2 ms, 60 % 2D / 40 % 3D, 10-100 steps) through the
+    serving loop: 120 GB admission budget, --serve-slots concurrent requests.
+    The payloads (mesh, phi, base field, c0) are built before the clock
+    starts; latency = finish - arrival, including queueing and the uploads."""
+    from paper_1908_05834_gb300 import serve
+    reqs = inputs.serving_requests(args.serve_requests)
+    t0 = time.perf_counter()
+    prepared = {r.rid: r.materialize() for r in reqs}
+    prep_s = time.perf_counter() - t0
+    opts = _serving_options(bchar, args)
+    srv = serve.Server(serve.GpuExecutor(prepared, opts, torch.cuda.current_device()),
+                       serve.estimator_for(prepared, opts), budget_bytes=120e9, max_active=args.serve_slots)
+    res = srv.run(reqs)
+    s = serve.summarize(res)
+    s.update({"unit": UNIT, "budget_gb": 120, "slots": args.serve_slots,
+              "peak_admitted_gb": round(srv.peak_used / 1e9, 2), "peak_active": srv.peak_active,
+              "max_peak_bytes_over_estimate": round(max((r.peak_bytes / r.est_bytes) for r in res
+                                                        if r.status == "ok"), 3),
+              "prep_s": round(prep_s, 1),
+              "sample": f"first {len(reqs)} of the 512-request serving stream (seed 4004), full step counts, "
+                        f"FP32 split, qp_tol {args.qp_tol}"})
+    return s
 
 
 def oracle_sample_step_rate(seconds: float):
@@ -348,6 +446,11 @@ def main():
     p.add_argument("--qp-max-iter", type=int, default=30000)
     p.add_argument("--qp-tol", type=float, default=1e-5)
     p.add_argument("--n", type=int, default=None, help="cells per axis (same recipe; for small profiling runs)")
+    p.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
+    p.add_argument("--batch-count", type=int, default=16)
+    p.add_argument("--batch-steps", type=int, default=3)
+    p.add_argument("--serve-requests", type=int, default=32)
+    p.add_argument("--serve-slots", type=int, default=32)
     args = p.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":

@@ -218,6 +218,51 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
 bchar_status bchar_mass_noalloc(const double *volphi, const void *c, int c_dtype, int64_t n, double *mass_out,
                                 void *stream);
 
+/* Like bchar_set_velocity, with every face velocity multiplied by `scale`
+ * (finite; 0 is allowed and stops the flow) on the device after the copy:
+ * for fields of the form u(x) g(t), the caller passes u once per step with
+ * the factor g(t^n + dt/2) and needs no scaled copy of its own.  The checks
+ * (boundary flux, divergence) apply to the scaled field.
+ * Errors: as bchar_set_velocity; INVALID_ARG for a non-finite scale. */
+bchar_status bchar_set_velocity_scaled(bchar_mesh_t m, const double *const face_u[3], int on_device, double scale);
+
+/* Device memory held by the handle now and at most so far (bytes; every
+ * buffer the library allocated for it).  Either pointer may be NULL, not both.
+ * Errors: INVALID_ARG. */
+bchar_status bchar_device_bytes(bchar_mesh_t m, int64_t *now, int64_t *peak);
+
+/* A-priori estimate (bytes) of the device memory a handle created with these
+ * arguments will hold after its steps, for admission control before any
+ * allocation: per cell (mesh arrays, minimisation vectors, row slab,
+ * multigrid), per ball (the tight packing, counted here from the widths)
+ * and per matrix entry, with the entries bounded by a 3^d neighbourhood per
+ * row (9 in 2D, 27 in 3D), plus 10 %.  A step whose rows grow wider than the
+ * slab's initial capacity (24 entries in 2D, 64 in 3D) holds more.  Host
+ * only; no GPU work.  coords as for bchar_create_mesh; opt NULL = defaults.
+ * Errors: INVALID_ARG. */
+bchar_status bchar_estimate_device_bytes(int dim, const int64_t n_cells[3], const double *const coords[3],
+                                         const bchar_options *opt, int64_t *bytes);
+
+/* One time step of `count` independent handles at once (the paper has no
+ * counterpart; it steps one mesh).  Instance i is bchar_step(meshes[i],
+ * dt[i], c_in[i], c_out[i], c_dtype[i], infos ? &infos[i] : NULL), with the
+ * same arguments, rules and result, bitwise; the instances run concurrently
+ * from up to max_workers host threads of the library (<= 0: 16), largest
+ * mesh first, each on its handle's own stream.  Give every handle its own
+ * stream: handles that share one still give correct results but run one after
+ * the other on the GPU.  The handles must be distinct (a handle is used by
+ * one thread at a time) and none may be in use elsewhere during the call.
+ * Returns when every instance has finished; the current device of the calling
+ * thread is kept.
+ *   statuses  HOST array of count statuses (nullable), one per instance
+ *   infos     HOST array of count bchar_step_info (nullable)
+ * Returns OK, or the first failing instance's status (in index order); the
+ * other instances still ran.  Errors: INVALID_ARG (count < 0, a NULL array or
+ * handle, a handle listed twice), CUDA, OUT_OF_MEMORY (host threads). */
+bchar_status bchar_step_batch(int count, const bchar_mesh_t *meshes, const double *dt, const void *const *c_in,
+                              void *const *c_out, const int *c_dtype, bchar_step_info *infos,
+                              bchar_status *statuses, int max_workers);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,14 @@ STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK, STAGE_SMOOTH = 0, 1,
 
 lib.bchar_mass_noalloc.argtypes = [_P, _P, ctypes.c_int, _I64, _P, _P]
 lib.bchar_mass_noalloc.restype = ctypes.c_int
+lib.bchar_set_velocity_scaled.argtypes = [_H, _P, ctypes.c_int, ctypes.c_double]
+lib.bchar_set_velocity_scaled.restype = ctypes.c_int
+lib.bchar_device_bytes.argtypes = [_H, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
+lib.bchar_device_bytes.restype = ctypes.c_int
+lib.bchar_estimate_device_bytes.argtypes = [ctypes.c_int, _P, _P, ctypes.POINTER(Options), ctypes.POINTER(_I64)]
+lib.bchar_estimate_device_bytes.restype = ctypes.c_int
+lib.bchar_step_batch.argtypes = [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]
+lib.bchar_step_batch.restype = ctypes.c_int
 
 bchar_default_options = lib.bchar_default_options
 bchar_create_mesh = lib.bchar_create_mesh
@@ -101,6 +109,10 @@ bchar_export_matrix = lib.bchar_export_matrix
 bchar_export_tracked = lib.bchar_export_tracked
 bchar_time_stage = lib.bchar_time_stage
 bchar_mass_noalloc = lib.bchar_mass_noalloc
+bchar_set_velocity_scaled = lib.bchar_set_velocity_scaled
+bchar_device_bytes = lib.bchar_device_bytes
+bchar_estimate_device_bytes = lib.bchar_estimate_device_bytes
+bchar_step_batch = lib.bchar_step_batch
 
 
 def default_options(**kw) -> Options:
@@ -149,8 +161,9 @@ class Mesh:
             detail = lib.bchar_last_error(self.handle)
             raise BcharError(st, f"{what}: {detail.decode() if detail else ''}")
 
-    def set_velocity(self, faces):
-        """faces: dim face-velocity arrays, numpy (host) or torch CUDA tensors (device)."""
+    def set_velocity(self, faces, scale: float = 1.0):
+        """faces: dim face-velocity arrays, numpy (host) or torch CUDA tensors (device);
+        the library multiplies them by ``scale`` on the device."""
         try:
             import torch
             on_device = isinstance(faces[0], torch.Tensor) and faces[0].is_cuda
@@ -162,7 +175,17 @@ class Mesh:
         else:
             self._faces_keep = [np.ascontiguousarray(f, dtype=np.float64).reshape(-1) for f in faces]
             ptrs = _ptr_array([f.ctypes.data for f in self._faces_keep])
-        self._check(lib.bchar_set_velocity(self.handle, ctypes.addressof(ptrs), int(on_device)), "set_velocity")
+        if scale == 1.0:
+            st = lib.bchar_set_velocity(self.handle, ctypes.addressof(ptrs), int(on_device))
+        else:
+            st = lib.bchar_set_velocity_scaled(self.handle, ctypes.addressof(ptrs), int(on_device), float(scale))
+        self._check(st, "set_velocity")
+
+    def device_bytes(self) -> tuple[int, int]:
+        """(bytes held now, peak) of the handle's device memory."""
+        now, peak = _I64(0), _I64(0)
+        self._check(lib.bchar_device_bytes(self.handle, ctypes.byref(now), ctypes.byref(peak)), "device_bytes")
+        return int(now.value), int(peak.value)
 
     def step(self, dt: float, c_in, c_out) -> dict:
         """One time step; c_in / c_out are torch CUDA tensors of n_c float64 or float32."""
@@ -221,3 +244,40 @@ class Mesh:
 
     def __exit__(self, *a):
         self.close()
+
+
+def estimate_device_bytes(coords, options: Options | None = None) -> int:
+    """A-priori device-memory estimate of a handle on this mesh (bchar_estimate_device_bytes)."""
+    coords = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
+    dim = len(coords)
+    n_cells = (ctypes.c_int64 * 3)(*([len(c) - 1 for c in coords] + [1] * (3 - dim)))
+    cptrs = _ptr_array([c.ctypes.data for c in coords])
+    out = _I64(0)
+    opt = options or default_options()
+    st = lib.bchar_estimate_device_bytes(dim, ctypes.addressof(n_cells), ctypes.addressof(cptrs), ctypes.byref(opt),
+                                         ctypes.byref(out))
+    if st != BCHAR_OK:
+        raise BcharError(st, "bchar_estimate_device_bytes")
+    return int(out.value)
+
+
+def step_batch(meshes, dts, c_ins, c_outs, max_workers: int = 0):
+    """One step of several handles at once (bchar_step_batch).  Returns
+    (infos, statuses); raises BcharError with the first failing status."""
+    import torch
+    k = len(meshes)
+    hs = (ctypes.c_void_p * k)(*[m.handle.value for m in meshes])
+    dt = (ctypes.c_double * k)(*[float(d) for d in dts])
+    ci = (ctypes.c_void_p * k)(*[c.data_ptr() for c in c_ins])
+    co = (ctypes.c_void_p * k)(*[c.data_ptr() for c in c_outs])
+    for m, a, b in zip(meshes, c_ins, c_outs):
+        assert a.is_cuda and b.is_cuda and a.dtype == b.dtype and a.numel() == b.numel() == m.nc
+    dty = (ctypes.c_int * k)(*[C_F64 if c.dtype == torch.float64 else C_F32 for c in c_ins])
+    infos = (StepInfo * k)()
+    sts = (ctypes.c_int * k)()
+    st = lib.bchar_step_batch(k, hs, dt, ci, co, dty, infos, sts, int(max_workers))
+    if st != BCHAR_OK:
+        bad = next(i for i in range(k) if sts[i] != BCHAR_OK) if any(sts[i] != BCHAR_OK for i in range(k)) else -1
+        detail = lib.bchar_last_error(meshes[bad].handle) if bad >= 0 else b""
+        raise BcharError(st, f"step_batch instance {bad}: {detail.decode() if detail else ''}")
+    return [infos[i].as_dict() for i in range(k)], [int(sts[i]) for i in range(k)]

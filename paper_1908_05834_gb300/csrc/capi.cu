@@ -17,9 +17,7 @@ bool ensure(bchar_mesh_t m, Buf &b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return true;
     if (b.p) {
         cudaStreamSynchronize(m->stream);  // the old buffer may still be read by queued work
-        cudaFree(b.p);
-        b.p = nullptr;
-        b.bytes = 0;
+        release(b);
     }
     const size_t want = bytes < 256 ? 256 : bytes;
     if (cudaMalloc(&b.p, want) != cudaSuccess) {
@@ -31,13 +29,18 @@ bool ensure(bchar_mesh_t m, Buf &b, size_t bytes) {
         return false;
     }
     b.bytes = want;
+    b.acct = &m->dev_bytes;
+    m->dev_bytes += static_cast<int64_t>(want);
+    if (m->dev_bytes > m->dev_bytes_peak) m->dev_bytes_peak = m->dev_bytes;
     return true;
 }
 
 void release(Buf &b) {
     if (b.p) cudaFree(b.p);
+    if (b.p && b.acct) *b.acct -= static_cast<int64_t>(b.bytes);
     b.p = nullptr;
     b.bytes = 0;
+    b.acct = nullptr;
 }
 
 MeshView full_view(bchar_mesh_t m) {
@@ -216,6 +219,11 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
     }
 
     bchar_mesh_t m = new bchar_mesh_s();
+    if (cudaGetDevice(&m->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return BCHAR_ERR_CUDA;
+    }
     m->dim = dim;
     m->nb = o.balls_per_axis;
     for (int a = 0; a < 3; ++a) m->n[a] = n[a];
@@ -309,7 +317,12 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
 }
 
 bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int on_device) {
+    return bchar_set_velocity_scaled(m, face_u, on_device, 1.0);
+}
+
+bchar_status bchar_set_velocity_scaled(bchar_mesh_t m, const double *const *face_u, int on_device, double scale) {
     if (!m) return BCHAR_ERR_INVALID_ARG;
+    if (!isfinite(scale)) return fail(m, BCHAR_ERR_INVALID_ARG, "scale must be finite");
     m->err.clear();
     if (!face_u) return fail(m, BCHAR_ERR_INVALID_ARG, "face_u is NULL");
     m->has_velocity = false;
@@ -323,6 +336,7 @@ bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int
         cudaMemcpyAsync(m->u[a].p, face_u[a], sizeof(double) * nf,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
     }
+    if (scale != 1.0) launch_scale_velocity(m, scale);
     cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
     launch_velocity_check(m);
     bchar_status st = read_info(m);
@@ -502,6 +516,60 @@ bchar_status bchar_export_tracked(bchar_mesh_t m, double *pos, double *rhat, int
     release(dpos);
     release(drh);
     return cuda_check(m);
+}
+
+bchar_status bchar_device_bytes(bchar_mesh_t m, int64_t *now, int64_t *peak) {
+    if (!m || (!now && !peak)) return BCHAR_ERR_INVALID_ARG;
+    if (now) *now = m->dev_bytes;
+    if (peak) *peak = m->dev_bytes_peak;
+    return BCHAR_OK;
+}
+
+bchar_status bchar_estimate_device_bytes(int dim, const int64_t *n_cells, const double *const *coords,
+                                         const bchar_options *opt, int64_t *bytes) {
+    if (!bytes || (dim != 2 && dim != 3) || !n_cells || !coords) return BCHAR_ERR_INVALID_ARG;
+    *bytes = 0;
+    bchar_options o;
+    bchar_default_options(&o);
+    if (opt) o = *opt;
+    if (!options_valid(o)) return BCHAR_ERR_INVALID_ARG;
+    int64_t n[3] = {1, 1, 1}, nc = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (n_cells[a] < 1 || n_cells[a] > (1 << 30) || !coords[a]) return BCHAR_ERR_INVALID_ARG;
+        n[a] = n_cells[a];
+        nc *= n[a];
+        if (nc > 0x7fffffffLL) return BCHAR_ERR_INVALID_ARG;
+    }
+    // balls: the tight packing of every cell (counted on the host from the widths)
+    int64_t nballs = 0;
+    for (int64_t k = 0; k < nc; ++k) {
+        const int64_t c[3] = {k % n[0], (k / n[0]) % n[1], k / (n[0] * n[1])};
+        double w[3] = {0, 0, 0}, wmin = INFINITY;
+        for (int a = 0; a < dim; ++a) {
+            w[a] = coords[a][c[a] + 1] - coords[a][c[a]];
+            if (!(w[a] > 0.0)) return BCHAR_ERR_INVALID_ARG;
+            wmin = w[a] < wmin ? w[a] : wmin;
+        }
+        int64_t cnt = 1;
+        for (int a = 0; a < dim; ++a) {
+            int64_t na = static_cast<int64_t>(floor(o.balls_per_axis * w[a] / wmin + 1e-9));
+            cnt *= na > o.balls_per_axis ? na : o.balls_per_axis;
+        }
+        nballs += cnt;
+    }
+    // bytes per cell, per ball and per matrix entry of every buffer a step holds:
+    // mesh and row arrays 116, minimisation vectors 2 x 11 x 8, union-find 80,
+    // face velocities 12 d, row slab 12 row_cap, matching scratch 48, multigrid
+    // level 0 144 and coarser levels ~154; per entry: CSR and column view 68,
+    // multigrid level 0 48 and coarser ~50; per ball 8 + 4 (3 + 1) x precision.
+    const int row_cap = dim == 2 ? 24 : 64;
+    const double per_cell = 116 + 176 + 80 + 12.0 * dim + 12.0 * row_cap + 48 + 144 + 154;
+    const double per_entry = 68 + 48 + 50;
+    const double per_ball = 8 + 4.0 * (o.precision == BCHAR_FP32_SPLIT ? 4 : 8);
+    const double nnz_bound = (dim == 2 ? 9.0 : 27.0) * nc;  // a 3^d neighbourhood per row
+    const double fixed = 4.0 * 152 * 64 * 8 + 4096 * 8 + (1 << 20);
+    *bytes = static_cast<int64_t>(1.1 * (per_cell * nc + per_entry * nnz_bound + per_ball * nballs + fixed));
+    return BCHAR_OK;
 }
 
 bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms) {

@@ -85,6 +85,7 @@ struct CgState {
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
+    int64_t *acct = nullptr;  // the owning handle's byte counter
 };
 
 // One level of the multigrid hierarchy: a symmetric CSR operator (off-diagonal
@@ -110,6 +111,9 @@ struct Amg {
 }  // namespace bchar
 
 struct bchar_mesh_s {
+    int device = 0;               // CUDA device current at create
+    int64_t dev_bytes = 0;        // device memory held now (every Buf of the handle)
+    int64_t dev_bytes_peak = 0;
     int dim = 0;
     int nb = 2;
     int64_t n[3] = {1, 1, 1};
@@ -177,6 +181,7 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 void launch_mesh_setup(bchar_mesh_t m);
 void launch_ball_cells(bchar_mesh_t m);
 void launch_velocity_check(bchar_mesh_t m);
+void launch_scale_velocity(bchar_mesh_t m, double scale);
 // track.cu
 void launch_track(bchar_mesh_t m, double dt, int substeps);
 void launch_seed_columns(bchar_mesh_t m, double dt, int substeps);

@@ -149,6 +149,19 @@ __global__ void k_to_float(const double *in, float *out, int64_t n) {
         out[i] = static_cast<float>(in[i]);
 }
 
+__global__ void k_scale(double *v, int64_t n, double scale) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        v[i] *= scale;
+}
+
+void launch_scale_velocity(bchar_mesh_t m, double scale) {
+    for (int a = 0; a < m->dim; ++a) {
+        k_scale<<<blocks_for(m->nface[a]), kThreads, 0, m->stream>>>(ptr<double>(m->u[a]), m->nface[a], scale);
+        ++m->launches;
+    }
+}
+
 void launch_velocity_check(bchar_mesh_t m) {
     MeshView mv = partial_view(m);
     VelView vv{};

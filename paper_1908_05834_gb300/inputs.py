@@ -89,23 +89,38 @@ def indicator_ball_average(coords, centre, radius: float, q: int = 16) -> np.nda
     """Cell averages of the indicator of |x - centre| < radius: 1 or 0 for cells
     wholly inside or outside, q^d-point midpoint rule for cut cells.  x fastest."""
     d = len(coords)
-    lo = np.meshgrid(*[c[:-1] for c in coords], indexing="ij")
-    hi = np.meshgrid(*[c[1:] for c in coords], indexing="ij")
-    near = np.zeros(lo[0].shape)
-    far = np.zeros(lo[0].shape)
+    lo1 = [np.asarray(c[:-1], dtype=np.float64) for c in coords]
+    hi1 = [np.asarray(c[1:], dtype=np.float64) for c in coords]
+
+    def along(v, a):  # a 1D per-axis array placed on axis a of the (n_0, ..., n_{d-1}) grid
+        shape = [1] * d
+        shape[a] = v.shape[0]
+        return v.reshape(shape)
+
+    near = np.zeros([len(v) for v in lo1])
+    far = np.zeros([len(v) for v in lo1])
     for a in range(d):
-        dlo = lo[a] - centre[a]
-        dhi = hi[a] - centre[a]
-        near += np.where((dlo <= 0) & (dhi >= 0), 0.0, np.minimum(dlo ** 2, dhi ** 2))
-        far += np.maximum(dlo ** 2, dhi ** 2)
+        dlo = lo1[a] - centre[a]
+        dhi = hi1[a] - centre[a]
+        near = near + along(np.where((dlo <= 0) & (dhi >= 0), 0.0, np.minimum(dlo ** 2, dhi ** 2)), a)
+        far = far + along(np.maximum(dlo ** 2, dhi ** 2), a)
     out = np.where(far <= radius ** 2, 1.0, 0.0)
-    cut = np.argwhere((near < radius ** 2) & (far > radius ** 2))
+    cut = (near < radius ** 2) & (far > radius ** 2)
+    idx = np.nonzero(cut)
     t = (np.arange(q) + 0.5) / q
-    for idx in cut:
-        pts = np.meshgrid(*[lo[a][tuple(idx)] + t * (hi[a][tuple(idx)] - lo[a][tuple(idx)]) for a in range(d)],
-                          indexing="ij")
-        r2 = sum((pts[a] - centre[a]) ** 2 for a in range(d))
-        out[tuple(idx)] = np.mean(r2 < radius ** 2)
+    # the q^d points of every cut cell at once: axis a varies along dimension 1 + a
+    sq = []
+    for a in range(d):
+        l, h = lo1[a][idx[a]], hi1[a][idx[a]]
+        p = l[:, None] + t[None, :] * (h - l)[:, None]
+        shape = [p.shape[0]] + [1] * d
+        shape[1 + a] = q
+        sq.append(((p - centre[a]) ** 2).reshape(shape))
+    r2 = sq[0]
+    for a in range(1, d):
+        r2 = r2 + sq[a]
+    inside = (r2 < radius ** 2).reshape(r2.shape[0], -1)
+    out[idx] = np.count_nonzero(inside, axis=1) / q ** d
     return np.ascontiguousarray(out.transpose(*reversed(range(d))).reshape(-1))
 
 
@@ -191,3 +206,71 @@ def workload(name: str, n: int | None = None, steps: int | None = None) -> Workl
 
 
 WORKLOADS = ("vortex2d_32", "vortex2d_1024", "deform3d_128", "deform3d_256")
+
+
+# ---------------------------------------------------------------- serving stream
+
+@dataclass
+class ServeRequest:
+    """One request of the serving stream: a small transport problem, run for
+    ``steps`` steps.  Arrays are built by ``materialize`` (problem data only)."""
+    rid: int
+    arrival_s: float         # offset from the start of the stream
+    dim: int
+    n: int                   # cells per axis (uniform mesh)
+    amplitude: float         # A: the field is A u(x) cos(pi t / T)
+    cfl: float
+    steps: int
+    phi_seed: int
+
+    @property
+    def nc(self) -> int:
+        return self.n ** self.dim
+
+    @property
+    def T(self) -> float:
+        return 1.0 if self.dim == 2 else 1.5
+
+    @property
+    def dt(self) -> float:
+        """dt = CFL h phi_min / (A U_max), U_max = 1 (2D) or 2 (3D), phi_min = 1 (2D) or 0.1 (3D)."""
+        h = 1.0 / self.n
+        phi_min, umax = (1.0, 1.0) if self.dim == 2 else (0.1, 2.0)
+        return self.cfl * h * phi_min / (self.amplitude * umax)
+
+    def time_factor(self, step: int) -> float:
+        """A cos(pi t / T) at the mid-step time of ``step``."""
+        return self.amplitude * math.cos(math.pi * (step + 0.5) * self.dt / self.T)
+
+    def materialize(self, q: int = 4):
+        """(coords, phi, base face velocities u(x), c0): the face arrays are the
+        unscaled field; step k uses them times ``time_factor(k)``."""
+        coords = [uniform_coords(self.n)] * self.dim
+        if self.dim == 2:
+            phi = np.ones(self.nc)
+            faces = vortex2d_faces(coords, 1.0)
+            c0 = indicator_ball_average(coords, (0.5, 0.75), 0.15, q)
+        else:
+            rng = np.random.Generator(np.random.PCG64(self.phi_seed))
+            phi = log_uniform_phi(rng, self.nc, 0.1, 0.3)
+            faces = deform3d_faces(coords, 1.0)
+            c0 = indicator_ball_average(coords, (0.35, 0.35, 0.35), 0.15, q)
+        return coords, phi, faces, c0
+
+
+def serving_requests(count: int = 512, seed: int = 4004, mean_gap_s: float = 0.002) -> list[ServeRequest]:
+    """The serving stream: Poisson arrivals (mean gap 2 ms); 60 % 2D requests,
+    N log-uniform in [64, 1024], phi = 1, the vortex field; 40 % 3D requests, N
+    log-uniform in [32, 160], phi log-uniform in [0.1, 0.3], the deformation
+    field; amplitude U[0.5, 2], CFL U[0.5, 4], 10-100 steps (uniform)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out, t = [], 0.0
+    for rid in range(count):
+        t += rng.exponential(mean_gap_s)
+        two_d = rng.uniform() < 0.6
+        lo, hi = (64, 1024) if two_d else (32, 160)
+        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        out.append(ServeRequest(rid=rid, arrival_s=t, dim=2 if two_d else 3, n=n,
+                                amplitude=float(rng.uniform(0.5, 2.0)), cfl=float(rng.uniform(0.5, 4.0)),
+                                steps=int(rng.integers(10, 101)), phi_seed=int(rng.integers(1, 2 ** 31))))
+    return out

@@ -1,0 +1,117 @@
+"""Host-side rules of the serving loop (no GPU): first-come first-served
+admission, the memory budget, the limit on running requests, rejection and
+failure isolation.  The executor is a fake that sleeps."""
+import threading
+import time
+from dataclasses import dataclass
+
+import pytest
+
+from paper_1908_05834_gb300 import serve
+from paper_1908_05834_gb300.inputs import serving_requests
+
+
+@dataclass
+class Req:
+    rid: int
+    arrival_s: float
+    nc: int
+    steps: int = 1
+    work_s: float = 0.02
+    fail: bool = False
+
+
+def fake_executor(running: list, lock: threading.Lock):
+    def run(req):
+        with lock:
+            running.append(req.rid)
+        time.sleep(req.work_s)
+        with lock:
+            running.remove(req.rid)
+        if req.fail:
+            raise RuntimeError("planted failure")
+        return {"c": [req.rid], "peak_bytes": req.nc}
+    return run
+
+
+def by_cells(req):
+    return req.nc
+
+
+def test_all_requests_answered_in_rid_order():
+    reqs = [Req(i, 0.001 * i, 100 + i) for i in range(12)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=1e9, max_active=4)
+    res = srv.run(reqs)
+    assert [r.rid for r in res] == list(range(12))
+    assert all(r.status == "ok" and r.c == [r.rid] for r in res)
+    assert all(r.finished_s >= r.admitted_s >= r.arrival_s - 1e-9 for r in res)
+
+
+def test_budget_and_slot_limits_hold():
+    running, lock = [], threading.Lock()
+    reqs = [Req(i, 0.0, nc) for i, nc in enumerate([40, 30, 30, 50, 10, 20, 60, 5, 25, 35])]
+    srv = serve.Server(fake_executor(running, lock), by_cells, budget_bytes=100, max_active=3)
+    res = srv.run(reqs)
+    assert all(r.status == "ok" for r in res)
+    assert srv.peak_used <= 100
+    assert all(used <= 100 for _, _, used in srv.admission_log)
+    assert srv.peak_active <= 3
+
+
+def test_first_come_first_served():
+    reqs = [Req(i, 0.002 * i, 10 + (i % 3) * 40) for i in range(10)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=100, max_active=2)
+    srv.run(reqs)
+    order = [rid for _, rid, _ in srv.admission_log]
+    assert order == sorted(order)  # admitted in arrival order: nobody overtakes
+
+
+def test_continuous_batching_fills_freed_slots():
+    # a long request and many short ones arriving together: the short ones
+    # flow through the other slot while the long one runs
+    reqs = [Req(0, 0.0, 1, work_s=0.3)] + [Req(i, 0.0, 1, work_s=0.02) for i in range(1, 9)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=1e9, max_active=2)
+    res = srv.run(reqs)
+    assert srv.peak_active == 2
+    long_done = res[0].finished_s
+    assert sum(r.finished_s < long_done for r in res[1:]) >= 6
+
+
+def test_oversize_rejected_and_failure_isolated():
+    reqs = [Req(0, 0.0, 500), Req(1, 0.0, 10, fail=True), Req(2, 0.0, 10)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=100, max_active=2)
+    res = srv.run(reqs)
+    assert res[0].status.startswith("rejected")
+    assert res[1].status.startswith("error") and "planted" in res[1].status
+    assert res[2].status == "ok"
+
+
+def test_waits_for_arrivals():
+    reqs = [Req(0, 0.0, 1, work_s=0.0), Req(1, 0.15, 1, work_s=0.0)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=10, max_active=4)
+    res = srv.run(reqs)
+    assert res[1].admitted_s >= 0.15 - 1e-3
+
+
+def test_summary_percentiles():
+    res = [serve.Result(i, 0.0, 0.0, 0.001 * (i + 1), 100, 2, 1) for i in range(100)]
+    s = serve.summarize(res)
+    assert s["ok"] == 100 and s["cell_steps"] == 100 * 100 * 2
+    assert abs(s["p50_ms"] - 50.5) < 1e-6 and abs(s["p99_ms"] - 99.01) < 1e-6
+
+
+def test_serving_stream_recipe():
+    rs = serving_requests(512)
+    assert len(rs) == 512
+    two = [r for r in rs if r.dim == 2]
+    three = [r for r in rs if r.dim == 3]
+    assert 0.5 < len(two) / 512 < 0.7
+    assert all(64 <= r.n <= 1024 for r in two) and all(32 <= r.n <= 160 for r in three)
+    assert all(10 <= r.steps <= 100 and 0.5 <= r.amplitude <= 2 and 0.5 <= r.cfl <= 4 for r in rs)
+    gaps = [b.arrival_s - a.arrival_s for a, b in zip(rs, rs[1:])]
+    assert all(g >= 0 for g in gaps) and 0.0015 < sum(gaps) / len(gaps) < 0.0025
+    # dt from the CFL: A U_max dt / (h phi_min) = CFL
+    for r in rs[:20]:
+        umax, phimin = (1.0, 1.0) if r.dim == 2 else (2.0, 0.1)
+        assert r.amplitude * umax * r.dt * r.n / phimin == pytest.approx(r.cfl, rel=1e-12)
+    assert serving_requests(8) == serving_requests(8)  # seeded

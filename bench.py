@@ -193,6 +193,7 @@ def run_ours(args, rank, world, local_rank):
     }
     torch.cuda.nvtx.range_pop()
     cg_mean = statistics.mean(i["cg_iters"] for i in infos)
+    step_stage_ms = {k: round(statistics.mean(i["ms_stage"][k] for i in infos), 3) for k in infos[0]["ms_stage"]}
     per_step_ms = {
         "smooth_level0": stage_ms["smooth"] * 2 * cg_mean,  # two sweeps of the finest level per V-cycle
         "cg_matvec": stage_ms["cg_matvec"] * cg_mean,
@@ -238,6 +239,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(statistics.mean(i["kernel_launches"] for i in infos) * args.steps) + 0,
         "roofline": roofline,
         "stage_ms_per_step": {k: round(v, 3) for k, v in per_step_ms.items()},
+        "step_stage_ms": step_stage_ms,
         "step_stats": {"cg_iters_mean": statistics.mean(i["cg_iters"] for i in infos),
                        "qp_converged": sum(i["qp_converged"] for i in infos),
                        "kkt_rel_max": max(i["kkt_rel"] for i in infos),

@@ -92,6 +92,13 @@ typedef struct {
     int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
     int32_t amg_coarsest;    /* unknowns on its coarsest level */
     int32_t unbalanced;      /* connected components whose local targets were rescaled (see bchar_step) */
+    /* Milliseconds on the handle's stream (CUDA events) per stage of this call:
+     * [0] tracking, [1] intersections and row assembly (with empty-column
+     * seeding), [2] compaction, column view and target balancing, [3] the N
+     * scalings, [4] the minimisation (multigrid set-up and CG), [5] bounds,
+     * column fix and W, [6] update and masses, [7] the whole call from the
+     * first to the last stage.  Host round trips inside a stage count in it. */
+    float ms_stage[8];
 } bchar_step_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -38,10 +38,15 @@ class StepInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("substeps", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
                 ("refines", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
                 ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32)]
+                ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32),
+                ("ms_stage", ctypes.c_float * 8)]
+
+    STAGES = ("track", "assemble", "columns_balance", "scaling", "minimise", "finalise", "update", "total")
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_stage"}
+        d["ms_stage"] = dict(zip(self.STAGES, (float(x) for x in self.ms_stage)))
+        return d
 
 
 class BcharError(RuntimeError):

@@ -51,6 +51,7 @@ MeshView full_view(bchar_mesh_t m) {
         v.x[a] = ptr<double>(m->x[a]);
         v.wd[a] = ptr<double>(m->wd[a]);
         v.wf[a] = ptr<float>(m->wf[a]);
+        v.wif[a] = ptr<float>(m->wif[a]);
     }
     v.nc = m->nc;
     v.phi = ptr<double>(m->phi);
@@ -73,6 +74,8 @@ VelView vel_view(bchar_mesh_t m) {
         v.u[a] = ptr<double>(m->u[a]);
         v.uf[a] = ptr<float>(m->uf[a]);
     }
+    v.recd = ptr<double>(m->rec);
+    v.recf = ptr<float>(m->rec);
     return v;
 }
 
@@ -169,9 +172,13 @@ void bchar_destroy(bchar_mesh_t m) {
         release(m->x[a]);
         release(m->wd[a]);
         release(m->wf[a]);
+        release(m->wif[a]);
         release(m->u[a]);
         release(m->uf[a]);
     }
+    release(m->rec);
+    for (cudaEvent_t e : m->stage_ev)
+        if (e) cudaEventDestroy(e);
     if (m->info_host.p) cudaFreeHost(m->info_host.p);
     amg_release(m->amg);
     delete m;
@@ -238,11 +245,11 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
     bool ok = true;
     for (int a = 0; a < dim; ++a) {
         ok = ok && ensure(m, m->x[a], sizeof(double) * (n[a] + 1)) && ensure(m, m->wd[a], sizeof(double) * n[a]) &&
-             ensure(m, m->wf[a], sizeof(float) * n[a]);
+             ensure(m, m->wf[a], sizeof(float) * n[a]) && ensure(m, m->wif[a], sizeof(float) * n[a]);
     }
     for (int a = dim; a < 3; ++a) {  // unit extent along the missing axis
         ok = ok && ensure(m, m->x[a], sizeof(double) * 2) && ensure(m, m->wd[a], sizeof(double)) &&
-             ensure(m, m->wf[a], sizeof(float));
+             ensure(m, m->wf[a], sizeof(float)) && ensure(m, m->wif[a], sizeof(float));
     }
     ok = ok && ensure(m, m->phi, sizeof(double) * nc) && ensure(m, m->phif, sizeof(float) * nc) &&
          ensure(m, m->volphi, sizeof(double) * nc) && ensure(m, m->rad, sizeof(double) * nc) &&
@@ -282,6 +289,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
         const float onef = 1.0f;
         cudaMemcpyAsync(m->wd[a].p, &one, sizeof one, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->wf[a].p, &onef, sizeof onef, cudaMemcpyHostToDevice, m->stream);
+        cudaMemcpyAsync(m->wif[a].p, &onef, sizeof onef, cudaMemcpyHostToDevice, m->stream);
     }
     int64_t nballs = 0;
     cudaMemcpyAsync(&nballs, ptr<int64_t>(m->ball_off) + nc, sizeof nballs, cudaMemcpyDeviceToHost, m->stream);
@@ -359,6 +367,9 @@ bchar_status bchar_set_velocity_scaled(bchar_mesh_t m, const double *const *face
         return fail(m, BCHAR_ERR_DIVERGENCE, msg);
     }
     m->vmax = bits_to_double(h->vmax_bits);
+    const size_t rec_bytes = (m->opt.precision == BCHAR_FP32_SPLIT ? sizeof(float) : sizeof(double)) * 8 * m->nc;
+    if (!ensure(m, m->rec, rec_bytes)) return BCHAR_ERR_OUT_OF_MEMORY;
+    launch_cell_records(m);
     m->has_velocity = true;
     return BCHAR_OK;
 }
@@ -372,10 +383,11 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     if (c_dtype != BCHAR_C_F64 && c_dtype != BCHAR_C_F32) return fail(m, BCHAR_ERR_INVALID_ARG, "bad c_dtype");
     if (!m->has_velocity) return fail(m, BCHAR_ERR_NO_VELOCITY, "bchar_set_velocity first");
     m->launches = 0;
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventRecord(ev0, m->stream);
+    if (!m->stage_ev[0])
+        for (cudaEvent_t &e : m->stage_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(m);
+    cudaEvent_t *ev = m->stage_ev;
+    cudaEventRecord(ev[0], m->stream);
 
     // substeps: the smallest s with dt * vmax / s <= cfl * hmin
     int substeps = m->opt.substeps;
@@ -386,6 +398,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     }
     cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
     launch_track(m, dt, substeps);
+    cudaEventRecord(ev[1], m->stream);
 
     // initial weights, row by row, into the slab; grow the slab if a row is wider
     DevInfo *h = host_info(m);
@@ -419,6 +432,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         if (h->err) return fail(m, BCHAR_ERR_CAPACITY, "a seeded row overflowed its slab row");
     }
 
+    cudaEventRecord(ev[2], m->stream);
     // CSR and its column view
     scan_i32_to_i64(m, ptr<int32_t>(m->row_len), ptr<int64_t>(m->row_ptr), m->nc);
     int64_t nnz = 0;
@@ -436,24 +450,27 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     launch_compact(m);
     launch_transpose(m);
     if (!launch_balance(m)) return BCHAR_ERR_OUT_OF_MEMORY;
+    cudaEventRecord(ev[3], m->stream);
 
     // N alternating scalings, the minimisation, bounds and column fix, update
     launch_scaling(m);
+    cudaEventRecord(ev[4], m->stream);
     int cg_iters = 0, refines = 0;
     launch_minimise(m, &cg_iters, &refines);
+    cudaEventRecord(ev[5], m->stream);
     launch_finalise(m);
+    cudaEventRecord(ev[6], m->stream);
     launch_update(m, c_in, c_out, c_dtype);
-    cudaEventRecord(ev1, m->stream);
+    cudaEventRecord(ev[7], m->stream);
     if ((st = read_info(m)) != BCHAR_OK) return st;
     if (h->err) {
         char msg[96];
         snprintf(msg, sizeof msg, "capacity error bits 0x%x", h->err);
         return fail(m, BCHAR_ERR_CAPACITY, msg);
     }
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
+    float ms_stage[8] = {};
+    for (int k = 0; k < 7; ++k) cudaEventElapsedTime(&ms_stage[k], ev[k], ev[k + 1]);
+    cudaEventElapsedTime(&ms_stage[7], ev[0], ev[7]);
     m->have_step = true;
     m->substeps = substeps;
     m->dt = dt;
@@ -478,8 +495,8 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->amg_levels = m->amg_levels;
         info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);
         info->unbalanced = h->unbalanced;
+        for (int k = 0; k < 8; ++k) info->ms_stage[k] = ms_stage[k];
     }
-    (void)ms;
     return BCHAR_OK;
 }
 

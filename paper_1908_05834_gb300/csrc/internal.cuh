@@ -36,6 +36,7 @@ struct MeshView {
     const double *x[3];     // node coordinates per axis
     const double *wd[3];    // cell widths per axis, FP64
     const float *wf[3];     // cell widths per axis, FP32
+    const float *wif[3];    // 1 / cell width per axis, FP32 (from the FP64 width)
     const double *phi;      // porosity per cell
     const float *phif;
     const double *volphi;   // |K|_phi
@@ -53,6 +54,11 @@ struct MeshView {
 struct VelView {
     const double *u[3];
     const float *uf[3];
+    // one record of 8 values per cell: the lower and upper face velocity of
+    // each axis (0 for a missing axis), then phi (FP64 records) or 1 / phi
+    // (FP32 records), then 0; a tracking stage reads one record
+    const double *recd;
+    const float *recf;
 };
 
 // Scalars produced on the device during a step, copied to the host once.
@@ -130,9 +136,10 @@ struct bchar_mesh_s {
     std::string err;
 
     // persistent mesh data
-    bchar::Buf x[3], wd[3], wf[3], phi, phif, volphi, rad, radf, rhophi, rhophif, cnt, ball_off, ball_cell;
+    bchar::Buf x[3], wd[3], wf[3], wif[3], phi, phif, volphi, rad, radf, rhophi, rhophif, cnt, ball_off, ball_cell;
     // velocity
-    bchar::Buf u[3], uf[3];
+    bchar::Buf u[3], uf[3], rec;  // face velocities; per-cell tracking records
+    cudaEvent_t stage_ev[8] = {};  // stage boundaries of bchar_step (created on first use)
     int64_t nface[3] = {0, 0, 0};
     bool has_velocity = false;
     double vmax = 0.0;
@@ -182,6 +189,7 @@ void launch_mesh_setup(bchar_mesh_t m);
 void launch_ball_cells(bchar_mesh_t m);
 void launch_velocity_check(bchar_mesh_t m);
 void launch_scale_velocity(bchar_mesh_t m, double scale);
+void launch_cell_records(bchar_mesh_t m);
 // track.cu
 void launch_track(bchar_mesh_t m, double dt, int substeps);
 void launch_seed_columns(bchar_mesh_t m, double dt, int substeps);

@@ -13,11 +13,12 @@
 
 namespace bchar {
 
-__global__ void k_widths(const double *x, double *wd, float *wf, int n) {
+__global__ void k_widths(const double *x, double *wd, float *wf, float *wif, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double w = x[i + 1] - x[i];
         wd[i] = w;
         wf[i] = static_cast<float>(w);
+        wif[i] = static_cast<float>(1.0 / w);
     }
 }
 
@@ -79,7 +80,8 @@ static MeshView partial_view(bchar_mesh_t m) {
 void launch_mesh_setup(bchar_mesh_t m) {
     for (int a = 0; a < m->dim; ++a) {
         k_widths<<<blocks_for(m->n[a]), kThreads, 0, m->stream>>>(ptr<double>(m->x[a]), ptr<double>(m->wd[a]),
-                                                                    ptr<float>(m->wf[a]), static_cast<int>(m->n[a]));
+                                                                    ptr<float>(m->wf[a]), ptr<float>(m->wif[a]),
+                                                                    static_cast<int>(m->n[a]));
         ++m->launches;
     }
     MeshView v = partial_view(m);
@@ -160,6 +162,43 @@ void launch_scale_velocity(bchar_mesh_t m, double scale) {
         k_scale<<<blocks_for(m->nface[a]), kThreads, 0, m->stream>>>(ptr<double>(m->u[a]), m->nface[a], scale);
         ++m->launches;
     }
+}
+
+// Per-cell tracking records (see VelView): FP64 records hold phi, FP32
+// records 1 / phi (formed in FP64), so that a FP32 stage multiplies.
+template <class real>
+__global__ void k_cell_records(MeshView m, VelView v, real *rec) {
+    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < m.nc;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int c[3];
+        split_cell(m, k, c);
+        real r[8] = {real(0), real(0), real(0), real(0), real(0), real(0), real(0), real(0)};
+        for (int a = 0; a < m.dim; ++a) {
+            int e[3] = {c[0], c[1], c[2]};
+            int64_t len[3] = {m.n[0], m.n[1], m.n[2]};
+            len[a] += 1;
+            const int64_t lo = e[0] + len[0] * (e[1] + len[1] * static_cast<int64_t>(e[2]));
+            e[a] += 1;
+            const int64_t hi = e[0] + len[0] * (e[1] + len[1] * static_cast<int64_t>(e[2]));
+            r[2 * a] = Real<real>::u(v, a)[lo];
+            r[2 * a + 1] = Real<real>::u(v, a)[hi];
+        }
+        r[6] = sizeof(real) == 8 ? static_cast<real>(m.phi[k]) : static_cast<real>(1.0 / m.phi[k]);
+        for (int q = 0; q < 8; ++q) rec[8 * k + q] = r[q];
+    }
+}
+
+MeshView full_view(bchar_mesh_t m);
+VelView vel_view(bchar_mesh_t m);
+
+void launch_cell_records(bchar_mesh_t m) {
+    MeshView mv = full_view(m);
+    VelView vv = vel_view(m);
+    if (m->opt.precision == BCHAR_FP32_SPLIT)
+        k_cell_records<float><<<blocks_for(m->nc), kThreads, 0, m->stream>>>(mv, vv, ptr<float>(m->rec));
+    else
+        k_cell_records<double><<<blocks_for(m->nc), kThreads, 0, m->stream>>>(mv, vv, ptr<double>(m->rec));
+    ++m->launches;
 }
 
 void launch_velocity_check(bchar_mesh_t m) {

@@ -27,6 +27,7 @@ template <class real>
 __device__ __forceinline__ void relocate(const MeshView &m, int a, int &c, real &xi) {
     const real *w = Real<real>::w(m, a);
     const int n = m.n[a];
+#pragma unroll 1
     for (int it = 0; it < 64; ++it) {  // one face per stage under the substep rule
         if (xi >= real(1)) {
             if (c >= n - 1) {
@@ -49,57 +50,114 @@ __device__ __forceinline__ void relocate(const MeshView &m, int a, int &c, real 
     xi = xi < real(0) ? real(0) : (xi > real(1) ? real(1) : xi);
 }
 
-__device__ __forceinline__ int64_t face_idx(const MeshView &m, int a, const int c[3], int f) {
-    int e[3] = {c[0], c[1], c[2]};
-    int64_t len[3] = {m.n[0], m.n[1], m.n[2]};
-    e[a] = f;
-    len[a] += 1;
-    return e[0] + len[0] * (e[1] + len[1] * static_cast<int64_t>(e[2]));
+// Arithmetic of one stage in the tracking precision.  FP64 divides by phi and
+// by the width (the operations of a plain evaluation of the RT0 field); FP32
+// multiplies by 1 / phi from the cell's record and by the FP32 table of
+// 1 / width (both formed from FP64 values).
+template <class real> struct Stage;
+template <> struct Stage<double> {
+    // r[0..5]: lower/upper face velocity per axis, r[6]: phi
+    static __device__ __forceinline__ void load(const VelView &v, int64_t k, double r[7]) {
+        const double2 *p = reinterpret_cast<const double2 *>(v.recd + 8 * k);
+        const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+        r[0] = a.x, r[1] = a.y, r[2] = b.x, r[3] = b.y, r[4] = c.x, r[5] = c.y, r[6] = d.x;
+    }
+    static __device__ __forceinline__ double per_phi(double u, double phi) { return u / phi; }
+    static __device__ __forceinline__ double per_width(const MeshView &m, int a, int c, double d) {
+        return d / m.wd[a][c];
+    }
+};
+template <> struct Stage<float> {
+    // r[0..5]: lower/upper face velocity per axis, r[6]: 1 / phi
+    static __device__ __forceinline__ void load(const VelView &v, int64_t k, float r[7]) {
+        const float4 *p = reinterpret_cast<const float4 *>(v.recf + 8 * k);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        r[0] = a.x, r[1] = a.y, r[2] = a.z, r[3] = a.w, r[4] = b.x, r[5] = b.y, r[6] = b.z;
+    }
+    static __device__ __forceinline__ float per_phi(float u, float inv_phi) { return u * inv_phi; }
+    static __device__ __forceinline__ float per_width(const MeshView &m, int a, int c, float d) {
+        return d * __ldg(m.wif[a] + c);
+    }
+};
+
+// Flat index of a cell (32-bit: meshes hold fewer than 2^31 cells).
+template <int DIM> __device__ __forceinline__ int64_t cell_of(const MeshView &m, const int (&c)[3]) {
+    return DIM == 2 ? c[0] + m.n[0] * c[1] : c[0] + m.n[0] * (c[1] + m.n[1] * c[2]);
 }
 
-template <class real>
-__device__ __forceinline__ void flow(const MeshView &m, const VelView &v, const int c[3], const real xi[3],
-                                     real sign, real f[3]) {
-    const real phi = Real<real>::phi(m, flat_cell(m, c));
-    f[0] = f[1] = f[2] = real(0);
-    for (int a = 0; a < m.dim; ++a) {
-        const real *U = Real<real>::u(v, a);
-        real lo = U[face_idx(m, a, c, c[a])];
-        real hi = U[face_idx(m, a, c, c[a] + 1)];
-        real u = lo + xi[a] * (hi - lo);
-        f[a] = sign * u / phi;
+// f = sign u(p) / phi(p) at the point (c, xi): one record load.  The axis
+// count is a template parameter so that every per-point array stays in
+// registers (all loops unroll).
+template <class real, int DIM>
+__device__ __forceinline__ void flow(const MeshView &m, const VelView &v, const int (&c)[3], const real (&xi)[3],
+                                     real sign, real (&f)[3]) {
+    real r[7];
+    Stage<real>::load(v, cell_of<DIM>(m, c), r);
+    f[2] = real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const real u = r[2 * a] + xi[a] * (r[2 * a + 1] - r[2 * a]);
+        f[a] = sign * Stage<real>::per_phi(u, r[6]);
     }
 }
 
 // (c2, x2) = (c, xi) moved by the physical displacement s * k.
-template <class real>
-__device__ __forceinline__ void moved(const MeshView &m, const int c[3], const real xi[3], real s, const real k[3],
-                                      int c2[3], real x2[3]) {
-    c2[0] = c[0], c2[1] = c[1], c2[2] = c[2];
-    x2[0] = xi[0], x2[1] = xi[1], x2[2] = xi[2];
-    for (int a = 0; a < m.dim; ++a) {
-        x2[a] = xi[a] + (s * k[a]) / Real<real>::w(m, a)[c[a]];
+template <class real, int DIM>
+__device__ __forceinline__ void moved(const MeshView &m, const int (&c)[3], const real (&xi)[3], real s,
+                                      const real (&k)[3], int (&c2)[3], real (&x2)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c2[a] = c[a];
+        x2[a] = xi[a];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        x2[a] = xi[a] + Stage<real>::per_width(m, a, c[a], s * k[a]);
         relocate<real>(m, a, c2[a], x2[a]);
     }
 }
 
-template <class real>
-__device__ void rk4(const MeshView &m, const VelView &v, int c[3], real xi[3], real h, int substeps, real sign) {
+template <class real, int DIM, int P>
+__device__ void rk4(const MeshView &m, const VelView &v, int (&c)[P][3], real (&xi)[P][3], real h, int substeps,
+                    real sign) {
+    const real half = real(0.5) * h;
     for (int st = 0; st < substeps; ++st) {
-        real k1[3], k2[3], k3[3], k4[3];
-        int c2[3];
-        real x2[3];
-        flow<real>(m, v, c, xi, sign, k1);
-        moved<real>(m, c, xi, real(0.5) * h, k1, c2, x2);
-        flow<real>(m, v, c2, x2, sign, k2);
-        moved<real>(m, c, xi, real(0.5) * h, k2, c2, x2);
-        flow<real>(m, v, c2, x2, sign, k3);
-        moved<real>(m, c, xi, h, k3, c2, x2);
-        flow<real>(m, v, c2, x2, sign, k4);
-        for (int a = 0; a < m.dim; ++a) {
-            real d = h / real(6) * (k1[a] + real(2) * k2[a] + real(2) * k3[a] + k4[a]);
-            xi[a] = xi[a] + d / Real<real>::w(m, a)[c[a]];
-            relocate<real>(m, a, c[a], xi[a]);
+        real acc[P][3], k[P][3], x2[P][3];
+        int c2[P][3];
+#pragma unroll
+        for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c[p], xi[p], sign, k[p]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[p][a] = k[p][a];
+            moved<real, DIM>(m, c[p], xi[p], half, k[p], c2[p], x2[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[p][a] = acc[p][a] + real(2) * k[p][a];
+            moved<real, DIM>(m, c[p], xi[p], half, k[p], c2[p], x2[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[p][a] = acc[p][a] + real(2) * k[p][a];
+            moved<real, DIM>(m, c[p], xi[p], h, k[p], c2[p], x2[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const real d = h / real(6) * (acc[p][a] + k[p][a]);
+                xi[p][a] = xi[p][a] + Stage<real>::per_width(m, a, c[p][a], d);
+                relocate<real>(m, a, c[p][a], xi[p][a]);
+            }
         }
     }
 }
@@ -110,100 +168,178 @@ __device__ __forceinline__ double position(const MeshView &m, int a, int c, real
     return m.x[a][c] + static_cast<double>(xi) * m.wd[a][c];
 }
 
-template <class real>
-__global__ void k_track(MeshView m, VelView v, real h, int substeps, int phi_const, int64_t nballs,
-                        int32_t *out_cell, real *out_xi, real *out_rhat) {
+// Start of ball b: its cell and the local coordinate of its centre.
+template <class real, int DIM>
+__device__ __forceinline__ void ball_start(const MeshView &m, int64_t b, int64_t &K, int (&c0)[3], real (&xi0)[3]) {
+    K = m.ball_cell[b];
+    const int s = static_cast<int>(b - m.ball_off[K]);
+    int cnt[3];
+    unpack_counts(m.cnt[K], cnt);
+    split_cell(m, K, c0);
+    const int sub[3] = {s % cnt[0], (s / cnt[0]) % cnt[1], s / (cnt[0] * cnt[1])};
+    xi0[0] = xi0[1] = xi0[2] = real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xi0[a] = (real(sub[a]) + real(0.5)) / real(cnt[a]);
+}
+
+// phi constant: r_hat = r_K, only the centres move; each thread tracks
+// kBallsPerThread balls side by side (the last group repeats its last ball).
+constexpr int kBallsPerThread = 4;
+
+template <class real, int DIM>
+__global__ void k_track_centres(MeshView m, VelView v, real h, int substeps, int64_t nballs, int32_t *out_cell,
+                                real *out_xi, real *out_rhat) {
+    const int64_t ngroups = (nballs + kBallsPerThread - 1) / kBallsPerThread;
+    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int c[kBallsPerThread][3];
+        real xi[kBallsPerThread][3];
+        int64_t Ks[kBallsPerThread];
+#pragma unroll
+        for (int p = 0; p < kBallsPerThread; ++p) {
+            int64_t b = g * kBallsPerThread + p;
+            if (b >= nballs) b = nballs - 1;
+            ball_start<real, DIM>(m, b, Ks[p], c[p], xi[p]);
+        }
+        rk4<real, DIM, kBallsPerThread>(m, v, c, xi, h, substeps, real(-1));
+#pragma unroll
+        for (int p = 0; p < kBallsPerThread; ++p) {
+            const int64_t b = g * kBallsPerThread + p;
+            if (b >= nballs) break;
+            out_cell[b] = static_cast<int32_t>(cell_of<DIM>(m, c[p]));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out_xi[3 * b + a] = xi[p][a];
+            out_rhat[b] = Real<real>::rad(m, Ks[p]);
+        }
+    }
+}
+
+// phi varying: the centre and the 2 DIM axis points C +- r e_a of one ball
+// are tracked side by side by one thread; r_hat = their mean distance.
+template <class real, int DIM>
+__global__ void k_track_balls(MeshView m, VelView v, real h, int substeps, int64_t nballs, int32_t *out_cell,
+                              real *out_xi, real *out_rhat) {
+    constexpr int P = 1 + 2 * DIM;
     for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < nballs;
          b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t K = m.ball_cell[b];
-        const int s = static_cast<int>(b - m.ball_off[K]);
-        int cnt[3], c0[3];
-        unpack_counts(m.cnt[K], cnt);
-        split_cell(m, K, c0);
-        const int sub[3] = {s % cnt[0], (s / cnt[0]) % cnt[1], s / (cnt[0] * cnt[1])};
-        real xi0[3] = {real(0), real(0), real(0)};
-        for (int a = 0; a < m.dim; ++a) xi0[a] = (real(sub[a]) + real(0.5)) / real(cnt[a]);
-        int c[3] = {c0[0], c0[1], c0[2]};
-        real xi[3] = {xi0[0], xi0[1], xi0[2]};
-        rk4<real>(m, v, c, xi, h, substeps, real(-1));
-        out_cell[b] = static_cast<int32_t>(flat_cell(m, c));
-        for (int a = 0; a < 3; ++a) out_xi[3 * b + a] = xi[a];
+        int64_t K;
+        int c0[3];
+        real xi0[3];
+        ball_start<real, DIM>(m, b, K, c0, xi0);
         const real r = Real<real>::rad(m, K);
-        if (phi_const) {
-            out_rhat[b] = r;
-            continue;
-        }
-        double sum = 0.0;
-        for (int a = 0; a < m.dim; ++a) {
-            for (int sg = -1; sg <= 1; sg += 2) {
-                int cc[3] = {c0[0], c0[1], c0[2]};
-                real xx[3] = {xi0[0], xi0[1], xi0[2]};
-                xx[a] = xi0[a] + real(sg) * r / Real<real>::w(m, a)[c0[a]];
-                rk4<real>(m, v, cc, xx, h, substeps, real(-1));
-                double d2 = 0.0;
-                for (int q = 0; q < m.dim; ++q) {
-                    double dq = position<real>(m, q, cc[q], xx[q]) - position<real>(m, q, c[q], xi[q]);
-                    d2 += dq * dq;
-                }
-                sum += sqrt(d2);
+        int c[P][3];
+        real xi[P][3];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                c[p][a] = c0[a];
+                xi[p][a] = xi0[a];
+            }
+            if (p > 0) {  // point p: axis (p - 1) / 2, sign - for odd p, + for even p
+                const int a = (p - 1) / 2;
+                const real sg = (p & 1) ? real(-1) : real(1);
+                xi[p][a] = xi0[a] + sg * r / Real<real>::w(m, a)[c0[a]];
             }
         }
-        out_rhat[b] = static_cast<real>(sum / (2.0 * m.dim));
+        rk4<real, DIM, P>(m, v, c, xi, h, substeps, real(-1));
+        out_cell[b] = static_cast<int32_t>(cell_of<DIM>(m, c[0]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out_xi[3 * b + a] = xi[0][a];
+        double sum = 0.0;
+#pragma unroll
+        for (int p = 1; p < P; ++p) {
+            double d2 = 0.0;
+#pragma unroll
+            for (int q = 0; q < DIM; ++q) {
+                const double dq = position<real>(m, q, c[p][q], xi[p][q]) - position<real>(m, q, c[0][q], xi[0][q]);
+                d2 += dq * dq;
+            }
+            sum += sqrt(d2);
+        }
+        out_rhat[b] = static_cast<real>(sum / (2.0 * DIM));
     }
 }
 
 MeshView full_view(bchar_mesh_t m);
 VelView vel_view(bchar_mesh_t m);
 
-void launch_track(bchar_mesh_t m, double dt, int substeps) {
+template <class real>
+static void track_in(bchar_mesh_t m, real h, int substeps, int32_t *cell, real *xi, real *rhat) {
     MeshView mv = full_view(m);
     VelView vv = vel_view(m);
-    const int blocks = blocks_for(m->nballs, 128);
-    if (m->opt.precision == BCHAR_FP32_SPLIT)
-        k_track<float><<<blocks, 128, 0, m->stream>>>(mv, vv, static_cast<float>(dt / substeps), substeps,
-                                                      m->phi_const, m->nballs, ptr<int32_t>(m->t_cell),
-                                                      ptr<float>(m->t_xi), ptr<float>(m->t_rhat));
-    else
-        k_track<double><<<blocks, 128, 0, m->stream>>>(mv, vv, dt / substeps, substeps, m->phi_const, m->nballs,
-                                                       ptr<int32_t>(m->t_cell), ptr<double>(m->t_xi),
-                                                       ptr<double>(m->t_rhat));
+    if (m->phi_const) {
+        const int64_t groups = (m->nballs + kBallsPerThread - 1) / kBallsPerThread;
+        if (m->dim == 2)
+            k_track_centres<real, 2><<<blocks_for(groups, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
+                                                                                      cell, xi, rhat);
+        else
+            k_track_centres<real, 3><<<blocks_for(groups, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
+                                                                                      cell, xi, rhat);
+    } else if (m->dim == 2) {
+        k_track_balls<real, 2><<<blocks_for(m->nballs, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
+                                                                                   cell, xi, rhat);
+    } else {
+        k_track_balls<real, 3><<<blocks_for(m->nballs, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
+                                                                                   cell, xi, rhat);
+    }
     ++m->launches;
+}
+
+void launch_track(bchar_mesh_t m, double dt, int substeps) {
+    if (m->opt.precision == BCHAR_FP32_SPLIT)
+        track_in<float>(m, static_cast<float>(dt / substeps), substeps, ptr<int32_t>(m->t_cell), ptr<float>(m->t_xi),
+                        ptr<float>(m->t_rhat));
+    else
+        track_in<double>(m, dt / substeps, substeps, ptr<int32_t>(m->t_cell), ptr<double>(m->t_xi),
+                         ptr<double>(m->t_rhat));
 }
 
 // Residing cells that no tracked ball reached (Sec 3.2 assumes there are
 // none): the centre of such a cell M_j is carried forward over dt (F_{+dt})
 // and M_j's whole porous volume is assigned to the cell K_i it lands in,
 // a_ij = |M_j|_phi.  Seeds are recorded as (i << 32 | j).
-template <class real>
+template <class real, int DIM>
 __global__ void k_seed_columns(MeshView m, VelView v, real h, int substeps, const int32_t *colcnt,
                                unsigned long long *seeds, DevInfo *info) {
     for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < m.nc;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         if (colcnt[j] != 0) continue;
-        int c[3];
-        split_cell(m, j, c);
-        real xi[3] = {real(0), real(0), real(0)};
-        for (int a = 0; a < m.dim; ++a) xi[a] = real(0.5);
-        rk4<real>(m, v, c, xi, h, substeps, real(1));
+        int c[1][3];
+        split_cell(m, j, c[0]);
+        real xi[1][3] = {{real(0), real(0), real(0)}};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) xi[0][a] = real(0.5);
+        rk4<real, DIM, 1>(m, v, c, xi, h, substeps, real(1));
         int slot = atomicAdd(&info->n_seeds, 1);
         if (slot < kMaxSeeds)
-            seeds[slot] = (static_cast<unsigned long long>(flat_cell(m, c)) << 32) | static_cast<unsigned long long>(j);
+            seeds[slot] =
+                (static_cast<unsigned long long>(flat_cell(m, c[0])) << 32) | static_cast<unsigned long long>(j);
         else
             atomicOr(&info->err, kErrSeeds);
     }
 }
 
+template <class real, int DIM>
+static void seed_in(bchar_mesh_t m, real h, int substeps) {
+    k_seed_columns<real, DIM><<<blocks_for(m->nc), kThreads, 0, m->stream>>>(
+        full_view(m), vel_view(m), h, substeps, ptr<int32_t>(m->colcnt), ptr<unsigned long long>(m->seeds),
+        ptr<DevInfo>(m->dinfo));
+}
+
 void launch_seed_columns(bchar_mesh_t m, double dt, int substeps) {
-    MeshView mv = full_view(m);
-    VelView vv = vel_view(m);
-    if (m->opt.precision == BCHAR_FP32_SPLIT)
-        k_seed_columns<float><<<blocks_for(m->nc), kThreads, 0, m->stream>>>(
-            mv, vv, static_cast<float>(dt / substeps), substeps, ptr<int32_t>(m->colcnt),
-            ptr<unsigned long long>(m->seeds), ptr<DevInfo>(m->dinfo));
-    else
-        k_seed_columns<double><<<blocks_for(m->nc), kThreads, 0, m->stream>>>(
-            mv, vv, dt / substeps, substeps, ptr<int32_t>(m->colcnt), ptr<unsigned long long>(m->seeds),
-            ptr<DevInfo>(m->dinfo));
+    const bool f32 = m->opt.precision == BCHAR_FP32_SPLIT;
+    if (m->dim == 2) {
+        if (f32)
+            seed_in<float, 2>(m, static_cast<float>(dt / substeps), substeps);
+        else
+            seed_in<double, 2>(m, dt / substeps, substeps);
+    } else {
+        if (f32)
+            seed_in<float, 3>(m, static_cast<float>(dt / substeps), substeps);
+        else
+            seed_in<double, 3>(m, dt / substeps, substeps);
+    }
     ++m->launches;
 }
 

@@ -136,10 +136,17 @@ def summarize(results: list[Result]) -> dict:
     start = min(r.arrival_s for r in ok)
     end = max(r.finished_s for r in ok)
     cell_steps = sum(r.cells * r.steps for r in ok)
-    return {"requests": len(results), "ok": len(ok), "cell_steps": int(cell_steps),
-            "makespan_s": round(end - start, 4), "cell_steps_per_s": round(cell_steps / (end - start), 1),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "max_ms": round(float(lat.max()), 3)}
+    out = {"requests": len(results), "ok": len(ok), "cell_steps": int(cell_steps),
+           "makespan_s": round(end - start, 4), "cell_steps_per_s": round(cell_steps / (end - start), 1),
+           "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "max_ms": round(float(lat.max()), 3)}
+    stages: dict[str, float] = {}
+    for r in ok:
+        for name, ms in r.extra.get("stage_ms", {}).items():
+            stages[name] = stages.get(name, 0.0) + ms
+    if stages:  # summed over requests (concurrent requests overlap, so the sum exceeds the makespan)
+        out["stage_ms_sum"] = {k: round(v, 1) for k, v in stages.items()}
+    return out
 
 
 # ---------------------------------------------------------------- the GPU executor
@@ -171,16 +178,19 @@ class GpuExecutor:
                 c = torch.from_numpy(np.ascontiguousarray(c0, dtype=np.float64)).to("cuda")
                 out = torch.empty_like(c)
                 iters = 0
+                stage_ms: dict[str, float] = {}
                 for k in range(req.steps):
                     mesh.set_velocity(fdev, scale=req.time_factor(k))
                     info = mesh.step(req.dt, c, out)
                     iters += info["cg_iters"]
+                    for name, ms in info["ms_stage"].items():
+                        stage_ms[name] = stage_ms.get(name, 0.0) + ms
                     c, out = out, c
                 host = c.cpu().numpy()
                 peak = mesh.device_bytes()[1]
             finally:
                 mesh.close()
-        return {"c": host, "peak_bytes": peak, "cg_iters": iters}
+        return {"c": host, "peak_bytes": peak, "cg_iters": iters, "stage_ms": stage_ms}
 
 
 def estimator_for(prepared: dict, options) -> Callable[[Any], int]:

@@ -85,15 +85,43 @@ __global__ void k_level0_fill(int64_t nc, const int64_t *row_ptr, const int32_t 
 }
 
 // ---------------------------------------------------------------- matching
+//
+// Neighbours are ranked by (weight class, edge hash): the class is the binary
+// exponent of the weight, so weights within a factor of two rank equal and a
+// symmetric hash of the edge decides between them.  Ranking by the exact
+// weight fails on smooth flows: the weights then grow monotonically along the
+// strong chains of the graph, every node points the same way and almost no
+// choice is mutual (on a uniform 261^2 mesh one level kept 92 % of its nodes).
+// Equal classes with hashed order put local maxima everywhere.
 
-// Heaviest strong neighbour (most negative off-diagonal with w_ij >=
-// kStrength sqrt(d_i d_j)), ties to the smaller index; with only_free, among
-// neighbours that are still unpaired.
+__device__ __forceinline__ uint32_t edge_hash(int64_t i, int64_t j) {
+    const uint64_t a = static_cast<uint64_t>(i < j ? i : j), b = static_cast<uint64_t>(i < j ? j : i);
+    uint64_t x = (a * 0x9E3779B1ull + b * 0x85EBCA77ull) & 0xFFFFFFFFull;
+    x ^= x >> 16;
+    x = (x * 0x7FEB352Dull) & 0xFFFFFFFFull;
+    x ^= x >> 15;
+    x = (x * 0x846CA68Bull) & 0xFFFFFFFFull;
+    x ^= x >> 16;
+    return static_cast<uint32_t>(x);
+}
+
+// Is neighbour j (weight w > 0) ranked above the current best (class bc, hash bh, index b)?
+__device__ __forceinline__ bool ranks_above(int64_t i, int32_t j, double w, int32_t b, int bc, uint32_t bh, int &cls,
+                                            uint32_t &hs) {
+    cls = ilogb(w);
+    hs = edge_hash(i, j);
+    return b < 0 || cls > bc || (cls == bc && (hs > bh || (hs == bh && j < b)));
+}
+
+// Top-ranked strong neighbour (off-diagonal weight w_ij = -l_ij > 0 with
+// w_ij >= kStrength sqrt(d_i d_j)); with only_free, among neighbours that are
+// still unpaired.
 __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
                            const int32_t *partner, int only_free, int32_t *best) {
     GRID_STRIDE(i, n) {
         int32_t b = -1;
-        double bw = 0.0;
+        int bc = 0;
+        uint32_t bh = 0;
         if (!only_free || partner[i] < 0) {
             const double di = diag[i];
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
@@ -101,10 +129,13 @@ __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, co
                 if (j == i) continue;
                 if (only_free && partner[j] >= 0) continue;
                 const double w = -val[e];
-                if (!(w >= kStrength * sqrt(di * diag[j]))) continue;
-                if (w > bw || (w == bw && w > 0.0 && j < b)) {
-                    bw = w;
+                if (!(w > 0.0) || !(w >= kStrength * sqrt(di * diag[j]))) continue;
+                int cls;
+                uint32_t hs;
+                if (ranks_above(i, j, w, b, bc, bh, cls, hs)) {
                     b = j;
+                    bc = cls;
+                    bh = hs;
                 }
             }
         }
@@ -120,26 +151,33 @@ __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
     }
 }
 
-// Attachment target of every node: its heaviest neighbour over all edges
-// (ties to the smaller index) when that edge carries at least kAttach of the
-// node's own diagonal, else -1.  The test is one-sided on purpose: a leaf
-// hanging off a hub by an edge that is strong for the leaf (most of its
-// diagonal) but weak for the hub should follow the hub.
+// Attachment target of every node: its top-ranked neighbour over all edges
+// when the node's heaviest edge carries at least kAttach of its own diagonal,
+// else -1.  The test is one-sided on purpose: a leaf hanging off a hub by an
+// edge that is strong for the leaf (most of its diagonal) but weak for the
+// hub should follow the hub.
 __global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
                                 const double *diag, int32_t *att) {
     GRID_STRIDE(i, n) {
         int32_t b = -1;
-        double bw = 0.0;
+        int bc = 0;
+        uint32_t bh = 0;
+        double wmax = 0.0;
         for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
             const int32_t j = col[e];
             if (j == i) continue;
             const double w = -val[e];
-            if (w > bw || (w == bw && w > 0.0 && j < b)) {
-                bw = w;
+            if (!(w > 0.0)) continue;
+            wmax = fmax(wmax, w);
+            int cls;
+            uint32_t hs;
+            if (ranks_above(i, j, w, b, bc, bh, cls, hs)) {
                 b = j;
+                bc = cls;
+                bh = hs;
             }
         }
-        att[i] = (b >= 0 && bw >= kAttach * diag[i]) ? b : -1;
+        att[i] = (b >= 0 && wmax >= kAttach * diag[i]) ? b : -1;
     }
 }
 

@@ -29,7 +29,9 @@
 //     ~1e-14 of the edge weights and the subtraction would cancel it away;
 //   - a symmetric V-cycle (one damped-Jacobi sweep before and after the
 //     coarse correction, Jacobi sweeps on the coarsest level) is applied as
-//     the preconditioner of the conjugate gradients.
+//     the preconditioner of the conjugate gradients; per level it takes three
+//     kernels (pre-smoothing fused with the residual, restriction,
+//     prolongation fused with post-smoothing).
 // Every sum runs in a fixed order, so the hierarchy and its application are
 // deterministic.
 #include <math.h>
@@ -376,6 +378,28 @@ template <class T> __global__ void k_flip_out(int64_t nc, const T *x, double inv
     }
 }
 
+// z = S x / scale, with the per-block partial sums of z.res and z.rp that
+// the conjugate gradients need next (one pass instead of two)
+template <class T>
+__global__ void k_flip_out_dots(int64_t nc, const T *x, double inv_scale, double *z, const double *res,
+                                const double *rp, double *pa, double *pb, const CgState *st) {
+    if (st && st->converged) return;
+    double a = 0.0, b = 0.0;
+    GRID_STRIDE(l, 2 * nc) {
+        const double v = static_cast<double>(x[l]) * inv_scale;
+        const double zl = l < nc ? v : -v;
+        z[l] = zl;
+        a += zl * res[l];
+        b += zl * rp[l];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+}
+
 // Relaxation weight of row i: kOmega, or 1 for a row without off-diagonal
 // entries (then one sweep solves its equation exactly).
 __device__ __forceinline__ double row_weight(const int64_t *ptr, int64_t i) {
@@ -387,18 +411,6 @@ template <class T>
 __global__ void k_jacobi0(int64_t n, const int64_t *ptr, const T *diag, const T *b, T *x, const CgState *st) {
     if (st && st->converged) return;
     GRID_STRIDE(i, n) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
-}
-
-// r = b - L x
-template <class T>
-__global__ void k_residual(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
-                           const T *b, T *r, const CgState *st) {
-    if (st && st->converged) return;
-    GRID_STRIDE(i, n) {
-        T s = diag[i] * x[i];
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * x[col[e]];
-        r[i] = b[i] - s;
-    }
 }
 
 // x_out = x + omega_i (b - L x) / diag
@@ -415,6 +427,50 @@ __global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, cons
     }
 }
 
+// Pre-smoothing from zero and the residual in one pass: x = omega_i b / diag,
+// r = b - L x.  A neighbour j has an edge, so its weight is kOmega and its x_j
+// is formed from b_j and d_j exactly as its owner forms it.
+template <class T>
+__global__ void k_presmooth_residual(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
+                                     const T *b, T *x, T *r, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) {
+        const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+        const T bi = b[i], di = diag[i];
+        const T xi = static_cast<T>(e1 == e0 ? 1.0 : kOmega) * bi / di;
+        x[i] = xi;
+        T s = di * xi;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t j = col[e];
+            s += val[e] * (static_cast<T>(kOmega) * b[j] / diag[j]);
+        }
+        r[i] = bi - s;
+    }
+}
+
+// Prolongation and post-smoothing in one pass: with x' = x + xc[agg] (the
+// coarse correction; nothing for a node without a coarse counterpart),
+// x_out = x' + omega_i (b - L x') / diag.  A neighbour's x'_j is formed as its
+// owner forms it (a neighbour has an edge, so it has a coarse counterpart).
+template <class T>
+__global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
+                                 const int32_t *agg, const T *xc, const T *x, const T *b, T *x_out,
+                                 const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) {
+        const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+        const int32_t I = agg[i];
+        const T xi = I >= 0 ? x[i] + xc[I] : x[i];
+        T s = diag[i] * xi;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t j = col[e];
+            s += val[e] * (x[j] + xc[agg[j]]);
+        }
+        const T om = static_cast<T>(e1 == e0 ? 1.0 : kOmega);
+        x_out[i] = xi + om * (b[i] - s) / diag[i];
+    }
+}
+
 template <class T>
 __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlist, const T *r, T *bc,
                            const CgState *st) {
@@ -423,14 +479,6 @@ __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlis
         T s = 0;
         for (int64_t k = mptr[I]; k < mptr[I + 1]; ++k) s += r[mlist[k]];
         bc[I] = s;
-    }
-}
-
-template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x, const CgState *st) {
-    if (st && st->converged) return;
-    GRID_STRIDE(i, n) {
-        const int32_t I = agg[i];
-        if (I >= 0) x[i] += xc[I];
     }
 }
 
@@ -623,23 +671,26 @@ template <> struct LevelBufs<double> {
 };
 
 // z = S V(S res) / scale: one V-cycle of the sign-flipped operator in precision T.
-template <class T> static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st) {
+template <class T>
+static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool b_ready,
+                   const double *rp, double *pa, double *pb) {
     using B = LevelBufs<T>;
     cudaStream_t s = m->stream;
     const int64_t nc = m->nc;
     AmgLevel &L0 = amg.levels[0];
-    k_flip_in<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, B::b(L0), st);
-    ++m->launches;
+    if (!b_ready) {
+        k_flip_in<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, B::b(L0), st);
+        ++m->launches;
+    }
     for (int l = 0; l < amg.nlev - 1; ++l) {  // down: pre-smooth from zero, residual, restrict
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
-        k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
-        k_residual<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
-                                              B::x(L), B::b(L), B::r(L), st);
+        k_presmooth_residual<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+                                                        B::diag(L), B::b(L), B::x(L), B::r(L), st);
         k_restrict<T><<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
                                                            B::b(C), st);
-        m->launches += 3;
+        m->launches += 2;
     }
     {  // coarsest: Jacobi sweeps from zero (an even number, so the result is in x)
         AmgLevel &L = amg.levels[amg.nlev - 1];
@@ -662,31 +713,47 @@ template <class T> static void vcycle(bchar_mesh_t m, Amg &amg, const double *re
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);
-        const int bl = blocks_for(L.n);
-        k_prolong<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
-        k_jacobi<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
-                                            B::x(L), B::b(L), B::x2(L), st);
-        m->launches += 2;
+        k_prolong_smooth<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                 B::val(L), B::diag(L), ptr<int32_t>(L.agg), xc,
+                                                                 B::x(L), B::b(L), B::x2(L), st);
+        ++m->launches;
     }
-    k_flip_out<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, amg.nlev > 1 ? B::x2(L0) : B::x(L0), 1.0 / amg.scale, z,
-                                                        st);
+    const T *x0 = amg.nlev > 1 ? B::x2(L0) : B::x(L0);
+    if (pa)
+        k_flip_out_dots<T><<<kRedBlocks, kThreads, 0, s>>>(nc, x0, 1.0 / amg.scale, z, res, rp, pa, pb, st);
+    else
+        k_flip_out<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, x0, 1.0 / amg.scale, z, st);
     ++m->launches;
 }
 
-// One FP32 smoothing sweep on the finest level (for timing).
+// One FP32 prolongation + post-smoothing pass on the finest level, as the
+// V-cycle runs it (for timing; with a single level, a plain sweep).
 void amg_smooth_once(bchar_mesh_t m, Amg &amg) {
     AmgLevel &L = amg.levels[0];
-    k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
-                                                                  ptr<float>(L.fval), ptr<float>(L.fdiag),
-                                                                  ptr<float>(L.fx), ptr<float>(L.fb),
-                                                                  ptr<float>(L.fx2), nullptr);
+    if (amg.nlev > 1) {
+        AmgLevel &C = amg.levels[1];
+        k_prolong_smooth<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(
+            L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<float>(L.fval), ptr<float>(L.fdiag),
+            ptr<int32_t>(L.agg), ptr<float>(C.fx2), ptr<float>(L.fx), ptr<float>(L.fb), ptr<float>(L.fx2), nullptr);
+    } else {
+        k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                      ptr<float>(L.fval), ptr<float>(L.fdiag),
+                                                                      ptr<float>(L.fx), ptr<float>(L.fb),
+                                                                      ptr<float>(L.fx2), nullptr);
+    }
 }
 
-void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32) {
+void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32, bool b_ready,
+               const double *rp, double *pa, double *pb) {
     if (fp32)
-        vcycle<float>(m, amg, res, z, st);
+        vcycle<float>(m, amg, res, z, st, b_ready, rp, pa, pb);
     else
-        vcycle<double>(m, amg, res, z, st);
+        vcycle<double>(m, amg, res, z, st, b_ready, rp, pa, pb);
+}
+
+void *amg_finest_rhs(Amg &amg, bool fp32) {
+    AmgLevel &L0 = amg.levels[0];
+    return fp32 ? static_cast<void *>(ptr<float>(L0.fb)) : static_cast<void *>(ptr<double>(L0.b));
 }
 
 }  // namespace bchar

@@ -58,12 +58,16 @@ template <class real> __device__ __forceinline__ real lens(int dim, real d, real
 }
 
 template <class real> struct BallSmem {
+    // (tracked ball, residing cell) pairs of one row held in shared memory
+    static constexpr int kPairCap = sizeof(real) == 4 ? 512 : 256;
     int c[kMaxBallsPerCell][3];   // tracked cell, per axis
     int lo[kMaxBallsPerCell][3];  // candidate box of cells
     int hi[kMaxBallsPerCell][3];
     real p[kMaxBallsPerCell][3];  // tracked centre relative to the lower corner of its cell
     real rh[kMaxBallsPerCell];
     real den[kMaxBallsPerCell];
+    int poff[kMaxBallsPerCell + 1];  // first pair of each ball
+    real S[kPairCap];                // pair weights, ball by ball, each ball's box in (z, y, x) order
 };
 
 // Sum over the balls of residing cell M (cell coordinates mc) of
@@ -82,6 +86,16 @@ __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc
         wM[a] = Real<real>::w(m, a)[mc[a]];
     }
     const real reach = rh + rM;
+    // every residing ball lies inside its cell, so a cell farther than the
+    // reach from the tracked centre holds no overlapping ball (the loop below
+    // would return exactly 0); the margin keeps the test conservative
+    real dist2 = real(0);
+    for (int a = 0; a < m.dim; ++a) {
+        const real g = o[a] > real(0) ? o[a] : (o[a] + wM[a] < real(0) ? -(o[a] + wM[a]) : real(0));
+        dist2 += g * g;
+    }
+    const real lim = reach * real(1.001);
+    if (dist2 > lim * lim) return real(0);
     real sum = real(0);
     for (int sz = 0; sz < cnt[2]; ++sz) {
         real dz = m.dim == 3 ? o[2] + (real(sz) + real(0.5)) * wM[2] / real(cnt[2]) : real(0);
@@ -95,6 +109,13 @@ __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc
         }
     }
     return sum;
+}
+
+// Local index of cell mc in the candidate box of ball s ((z, y, x) order).
+template <class real>
+__device__ __forceinline__ int box_index(const BallSmem<real> &sm, int s, const int mc[3]) {
+    const int wx = sm.hi[s][0] - sm.lo[s][0] + 1, wy = sm.hi[s][1] - sm.lo[s][1] + 1;
+    return ((mc[2] - sm.lo[s][2]) * wy + (mc[1] - sm.lo[s][1])) * wx + (mc[0] - sm.lo[s][0]);
 }
 
 template <class real>
@@ -118,6 +139,8 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
             }
             continue;
         }
+        // 1. each lane s < nK: its tracked ball's cell, centre, radius and box of candidate cells
+        int box = 0;
         if (lane < nK) {
             const int64_t b = off + lane;
             int c[3];
@@ -151,16 +174,49 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
             }
             sm.p[lane][2] = p[2];
             sm.rh[lane] = rh;
+            box = (sm.hi[lane][0] - sm.lo[lane][0] + 1) * (sm.hi[lane][1] - sm.lo[lane][1] + 1) *
+                  (sm.hi[lane][2] - sm.lo[lane][2] + 1);
+        }
+        // 2. pair offsets: exclusive scan of the box sizes over the lanes
+        int incl = box;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int npairs = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane <= nK) sm.poff[lane] = incl - box;  // lane nK holds the total
+        __syncwarp();
+        const bool table = npairs <= BallSmem<real>::kPairCap;  // warp-uniform
+        // 3. every pair's weight once, spread over all lanes; then each
+        //    ball's denominator as the sum over its pairs in box order
+        if (table) {
+            for (int q = lane; q < npairs; q += 32) {
+                int s = 0;
+                while (s + 1 < nK && sm.poff[s + 1] <= q) ++s;
+                const int t = q - sm.poff[s];
+                const int wx = sm.hi[s][0] - sm.lo[s][0] + 1, wy = sm.hi[s][1] - sm.lo[s][1] + 1;
+                int mc[3] = {sm.lo[s][0] + t % wx, sm.lo[s][1] + (t / wx) % wy, sm.lo[s][2] + t / (wx * wy)};
+                sm.S[q] = ball_cell_weight<real>(m, sm.c[s], sm.p[s], sm.rh[s], mc, flat_cell(m, mc));
+            }
+            __syncwarp();
+            if (lane < nK) {
+                real den = real(0);
+                for (int q = sm.poff[lane]; q < sm.poff[lane + 1]; ++q) den += sm.S[q];
+                sm.den[lane] = den;
+                if (den == real(0)) atomicAdd(&info->void_balls, 1);
+            }
+        } else if (lane < nK) {  // too many pairs for the table: the ball's lane sums its own box
             real den = real(0);
             int mc[3];
             for (mc[2] = sm.lo[lane][2]; mc[2] <= sm.hi[lane][2]; ++mc[2])
                 for (mc[1] = sm.lo[lane][1]; mc[1] <= sm.hi[lane][1]; ++mc[1])
                     for (mc[0] = sm.lo[lane][0]; mc[0] <= sm.hi[lane][0]; ++mc[0])
-                        den += ball_cell_weight<real>(m, c, p, rh, mc, flat_cell(m, mc));
+                        den += ball_cell_weight<real>(m, sm.c[lane], sm.p[lane], sm.rh[lane], mc, flat_cell(m, mc));
             sm.den[lane] = den;
             if (den == real(0)) atomicAdd(&info->void_balls, 1);
         }
         __syncwarp();
+        // 4. the union box of the row, one residing cell per lane
         int LO[3], HI[3];
         for (int a = 0; a < 3; ++a) {
             LO[a] = sm.lo[0][a];
@@ -196,7 +252,8 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
                     for (int a = 0; a < m.dim; ++a) in = in && mc[a] >= sm.lo[s][a] && mc[a] <= sm.hi[s][a];
                     if (!in) continue;
                     if (sm.den[s] > real(0)) {
-                        real S = ball_cell_weight<real>(m, sm.c[s], sm.p[s], sm.rh[s], mc, M);
+                        const real S = table ? sm.S[sm.poff[s] + box_index(sm, s, mc)]
+                                             : ball_cell_weight<real>(m, sm.c[s], sm.p[s], sm.rh[s], mc, M);
                         V += mK * static_cast<double>(S / sm.den[s]);
                     } else if (mc[0] == sm.c[s][0] && mc[1] == sm.c[s][1] && mc[2] == sm.c[s][2]) {
                         V += mK;

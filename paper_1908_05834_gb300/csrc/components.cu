@@ -80,14 +80,26 @@ __global__ void k_uf_label(int64_t n2, int32_t *parent, int32_t *label) {
 }
 
 // Node l < n_c is row l, node n_c + j column j; both carry |.|_phi of their cell.
+// The lanes of a warp that add into the same slot are summed first (integer
+// limbs, so the order does not matter) and their leader adds once: one large
+// component would otherwise serialise every node on the same two counters.
 __global__ void k_comp_sums(int64_t nc, const int32_t *label, const double *volphi, int shift,
                             unsigned long long *acc) {
     GRID_STRIDE(l, 2 * nc) {
         const double b = volphi[l < nc ? l : l - nc];
         const unsigned long long q = static_cast<unsigned long long>(ldexp(b, shift));  // < 2^52, exact
-        const int64_t slot = 4 * static_cast<int64_t>(label[l]) + (l < nc ? 0 : 2);
-        atomicAdd(&acc[slot], q >> 26);
-        atomicAdd(&acc[slot + 1], q & ((1ull << 26) - 1));
+        const long long slot = 4 * static_cast<long long>(label[l]) + (l < nc ? 0 : 2);
+        const unsigned peers = __match_any_sync(__activemask(), slot);
+        unsigned long long hi = 0, lo = 0;
+        for (unsigned rest = peers; rest; rest &= rest - 1) {
+            const int src = __ffs(rest) - 1;
+            hi += __shfl_sync(peers, q >> 26, src);
+            lo += __shfl_sync(peers, q & ((1ull << 26) - 1), src);
+        }
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicAdd(&acc[slot], hi);
+            atomicAdd(&acc[slot + 1], lo);
+        }
     }
 }
 

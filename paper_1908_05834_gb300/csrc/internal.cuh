@@ -176,6 +176,10 @@ double total_volphi(bchar_mesh_t m);  // sum of |K|_phi over the mesh
 
 template <class T> inline T *ptr(Buf &b) { return static_cast<T *>(b.p); }
 
+// Blocks of the reduction kernels of the conjugate gradients (grid-stride;
+// one partial sum per block).
+constexpr int kRedBlocks = 152 * 8;
+
 inline int blocks_for(int64_t n, int threads = kThreads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

@@ -114,7 +114,10 @@ __device__ __forceinline__ int64_t face_index(const MeshView &m, int a, const in
 // largest |u| and |u.n| on boundary faces (u.n = 0 on the boundary, Sec 1),
 // and the net flux relative to the total flux through its faces
 // (div u = 0, Sec 2.2).
+// The four maxima are kept per thread, reduced per block and written with one
+// atomic per block (per-cell atomics on four shared counters serialise).
 __global__ void k_velocity_check(MeshView m, VelView v, DevInfo *info) {
+    double t_vmax = 0.0, t_umax = 0.0, t_bflux = 0.0, t_div = 0.0;
     for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < m.nc;
          k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         int c[3];
@@ -138,10 +141,20 @@ __global__ void k_velocity_check(MeshView m, VelView v, DevInfo *info) {
             atomicOr(&info->nonfinite, 1);
             continue;
         }
-        atomic_max_nonneg(&info->vmax_bits, umax / m.phi[k]);
-        atomic_max_nonneg(&info->umax_bits, umax);
-        atomic_max_nonneg(&info->bflux_bits, bflux);
-        atomic_max_nonneg(&info->div_bits, tot > 0.0 ? fabs(net) / tot : 0.0);
+        t_vmax = fmax(t_vmax, umax / m.phi[k]);
+        t_umax = fmax(t_umax, umax);
+        t_bflux = fmax(t_bflux, bflux);
+        t_div = fmax(t_div, tot > 0.0 ? fabs(net) / tot : 0.0);
+    }
+    t_vmax = block_max(t_vmax);
+    t_umax = block_max(t_umax);
+    t_bflux = block_max(t_bflux);
+    t_div = block_max(t_div);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(&info->vmax_bits, t_vmax);
+        atomic_max_nonneg(&info->umax_bits, t_umax);
+        atomic_max_nonneg(&info->bflux_bits, t_bflux);
+        atomic_max_nonneg(&info->div_bits, t_div);
     }
 }
 

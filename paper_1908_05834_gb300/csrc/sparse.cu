@@ -380,6 +380,28 @@ __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double
     if (threadIdx.x == 0) partials[blockIdx.x] = l1;
 }
 
+// The same, also writing the next V-cycle's right-hand side b = S res in its
+// precision T (S: +1 rows, -1 columns), so that the V-cycle needs no pass of
+// its own over res.
+template <class T>
+__global__ void k_cg_update_b(int64_t nc, const double *p, const double *q, double *d, double *res, double *rp,
+                              double *partials, T *b, const CgState *st) {
+    if (st->converged) return;
+    const double alpha = st->alpha;
+    double l1 = 0.0;
+    GRID_STRIDE(l, 2 * nc) {
+        d[l] += alpha * p[l];
+        const double r0 = res[l];
+        rp[l] = r0;
+        const double r = r0 - alpha * q[l];
+        res[l] = r;
+        b[l] = static_cast<T>(l < nc ? r : -r);
+        l1 += fabs(r);
+    }
+    l1 = block_sum(l1);
+    if (threadIdx.x == 0) partials[blockIdx.x] = l1;
+}
+
 // partial sums of z.res and z.rp (flexible, Polak-Ribiere form of beta: the
 // preconditioner may differ slightly between applications)
 __global__ void k_dot2(int64_t n, const double *z, const double *res, const double *rp, double *pa, double *pb,
@@ -435,9 +457,11 @@ __global__ void k_qp_accumulate(int64_t nc, const int64_t *row_ptr, const int32_
     }
 }
 
-static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res, double *z, const CgState *st) {
+static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res, double *z, const CgState *st,
+                         bool b_ready = false, const double *rp = nullptr, double *pa = nullptr,
+                         double *pb = nullptr) {
     if (amg) {
-        amg_apply(m, m->amg, res, z, st, fp32);
+        amg_apply(m, m->amg, res, z, st, fp32, b_ready, rp, pa, pb);
     } else {
         k_jacobi_precond<<<blocks_for(2 * m->nc), kThreads, 0, m->stream>>>(2 * m->nc, ptr<double>(m->diag), res, z, st);
         ++m->launches;
@@ -515,8 +539,8 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         }
         exec_fp32 = fp32;
         precondition(m, amg, fp32, res, z, nullptr);
-        k_dot<<<bl, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
-        k_cg_start<<<1, 1024, 0, s>>>(part_rz, bl, inner, st);
+        k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
+        k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, inner, st);
         k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
         m->launches += 4;
         // one batch of iterations is captured once into a CUDA graph and
@@ -524,16 +548,30 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         const int batch = amg ? 8 : 32;
         auto enqueue_batch = [&]() {
             for (int k = 0; k < batch; ++k) {
-                k_cg_matvec<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                   ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag,
-                                                   p, q, part, st);
-                k_cg_alpha<<<1, 1024, 0, s>>>(part, bl, st);
-                k_cg_update<<<bl, kThreads, 0, s>>>(n2, p, q, d, res, rp, part_l1, st);
-                precondition(m, amg, fp32, res, z, st);
-                k_dot2<<<bl, kThreads, 0, s>>>(n2, z, res, rp, part_rz, part_zp, st);
-                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_zp, part_l1, bl, st);
+                k_cg_matvec<<<kRedBlocks, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                                                           ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2,
+                                                           a2c, diag, p, q, part, st);
+                k_cg_alpha<<<1, 1024, 0, s>>>(part, kRedBlocks, st);
+                if (amg) {
+                    // the update also writes the V-cycle's right-hand side; the
+                    // V-cycle's last kernel also forms the two dot products
+                    if (fp32)
+                        k_cg_update_b<float><<<kRedBlocks, kThreads, 0, s>>>(
+                            nc, p, q, d, res, rp, part_l1, static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
+                    else
+                        k_cg_update_b<double><<<kRedBlocks, kThreads, 0, s>>>(
+                            nc, p, q, d, res, rp, part_l1, static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
+                    precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
+                    m->launches += 3;
+                } else {
+                    k_cg_update<<<kRedBlocks, kThreads, 0, s>>>(n2, p, q, d, res, rp, part_l1, st);
+                    precondition(m, amg, fp32, res, z, st);
+                    k_dot2<<<kRedBlocks, kThreads, 0, s>>>(n2, z, res, rp, part_rz, part_zp, st);
+                    m->launches += 4;
+                }
+                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_zp, part_l1, kRedBlocks, st);
                 k_cg_pupdate<<<bl, kThreads, 0, s>>>(n2, z, p, st);
-                m->launches += 6;
+                m->launches += 2;
             }
         };
         if (!exec) {

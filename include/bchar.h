@@ -190,7 +190,7 @@ enum {
     BCHAR_STAGE_UPDATE = 1,    /* c^{n+1} = W c^n and the mass sums */
     BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
     BCHAR_STAGE_TRACK = 3,     /* RK4 tracking of all balls */
-    BCHAR_STAGE_SMOOTH = 4     /* the multigrid's finest level in FP32: prolongation + damped-Jacobi sweep */
+    BCHAR_STAGE_SMOOTH = 4     /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
 };
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of

@@ -55,6 +55,7 @@ constexpr double kOmega = 0.6;        // Jacobi damping (rows with off-diagonal 
 constexpr double kStrength = 0.05;    // strong edge: w_ij >= kStrength sqrt(d_i d_j)
 constexpr double kAttach = 0.25;      // a leftover node follows an edge carrying this share of its diagonal
 constexpr int kCoarsestSweeps = 40;   // one-block coarsest solve
+constexpr int64_t kFuseBelow = 1 << 19;  // levels smaller than this fuse prolongation with smoothing
 constexpr int kLargeCoarsestSweeps = 20;
 
 // ---------------------------------------------------------------- level 0
@@ -482,6 +483,14 @@ __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlis
     }
 }
 
+template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x, const CgState *st) {
+    if (st && st->converged) return;
+    GRID_STRIDE(i, n) {
+        const int32_t I = agg[i];
+        if (I >= 0) x[i] += xc[I];
+    }
+}
+
 // Coarsest level: kCoarsestSweeps damped-Jacobi sweeps from zero, all in one
 // block (the level is small), double-buffered in global memory.
 template <class T>
@@ -713,10 +722,17 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);
-        k_prolong_smooth<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
-                                                                 B::val(L), B::diag(L), ptr<int32_t>(L.agg), xc,
-                                                                 B::x(L), B::b(L), B::x2(L), st);
-        ++m->launches;
+        if (L.n < kFuseBelow) {  // launch-bound levels: one kernel
+            k_prolong_smooth<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                     B::val(L), B::diag(L), ptr<int32_t>(L.agg), xc,
+                                                                     B::x(L), B::b(L), B::x2(L), st);
+            ++m->launches;
+        } else {  // large levels: the sweep's neighbours read one array instead of three
+            k_prolong<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
+            k_jacobi<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+                                                             B::diag(L), B::x(L), B::b(L), B::x2(L), st);
+            m->launches += 2;
+        }
     }
     const T *x0 = amg.nlev > 1 ? B::x2(L0) : B::x(L0);
     if (pa)
@@ -726,21 +742,14 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
     ++m->launches;
 }
 
-// One FP32 prolongation + post-smoothing pass on the finest level, as the
-// V-cycle runs it (for timing; with a single level, a plain sweep).
+// One FP32 damped-Jacobi sweep on the finest level (for timing; on a large
+// finest level this is the V-cycle's post-smoothing kernel).
 void amg_smooth_once(bchar_mesh_t m, Amg &amg) {
     AmgLevel &L = amg.levels[0];
-    if (amg.nlev > 1) {
-        AmgLevel &C = amg.levels[1];
-        k_prolong_smooth<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(
-            L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<float>(L.fval), ptr<float>(L.fdiag),
-            ptr<int32_t>(L.agg), ptr<float>(C.fx2), ptr<float>(L.fx), ptr<float>(L.fb), ptr<float>(L.fx2), nullptr);
-    } else {
-        k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
-                                                                      ptr<float>(L.fval), ptr<float>(L.fdiag),
-                                                                      ptr<float>(L.fx), ptr<float>(L.fb),
-                                                                      ptr<float>(L.fx2), nullptr);
-    }
+    k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                  ptr<float>(L.fval), ptr<float>(L.fdiag),
+                                                                  ptr<float>(L.fx), ptr<float>(L.fb),
+                                                                  ptr<float>(L.fx2), nullptr);
 }
 
 void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32, bool b_ready,

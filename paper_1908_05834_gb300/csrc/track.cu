@@ -215,49 +215,67 @@ __global__ void k_track_centres(MeshView m, VelView v, real h, int substeps, int
 }
 
 // phi varying: the centre and the 2 DIM axis points C +- r e_a of one ball
-// are tracked side by side by one thread; r_hat = their mean distance.
+// are tracked by 1 + 2 DIM adjacent lanes, one point per lane (a small
+// single-point RK4, so few registers and many warps per SM); the lanes then
+// exchange positions by shuffles and the centre's lane forms r_hat, the mean
+// distance, summing the axis points in order.
 template <class real, int DIM>
 __global__ void k_track_balls(MeshView m, VelView v, real h, int substeps, int64_t nballs, int32_t *out_cell,
                               real *out_xi, real *out_rhat) {
-    constexpr int P = 1 + 2 * DIM;
-    for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < nballs;
-         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    constexpr int G = 1 + 2 * DIM;   // lanes (points) per ball
+    constexpr int PER_WARP = 32 / G;  // balls per warp
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G, p = lane % G;
+    const int base = g * G;
+    const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t nw_needed = (nballs + PER_WARP - 1) / PER_WARP;
+    for (int64_t w = warp; w < nw_needed; w += nwarps) {  // warp-uniform loop
+        int64_t b = w * PER_WARP + g;
+        const bool valid = g < PER_WARP && b < nballs;
+        if (!valid) b = nballs - 1;  // idle lanes track a copy and write nothing
         int64_t K;
         int c0[3];
         real xi0[3];
         ball_start<real, DIM>(m, b, K, c0, xi0);
         const real r = Real<real>::rad(m, K);
-        int c[P][3];
-        real xi[P][3];
+        int c[1][3] = {{c0[0], c0[1], c0[2]}};
+        real xi[1][3] = {{xi0[0], xi0[1], xi0[2]}};
+        {  // point p > 0: axis (p - 1) / 2, sign - for odd p, + for even p
+            const real sg = (p & 1) ? real(-1) : real(1);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                c[p][a] = c0[a];
-                xi[p][a] = xi0[a];
-            }
-            if (p > 0) {  // point p: axis (p - 1) / 2, sign - for odd p, + for even p
-                const int a = (p - 1) / 2;
-                const real sg = (p & 1) ? real(-1) : real(1);
-                xi[p][a] = xi0[a] + sg * r / Real<real>::w(m, a)[c0[a]];
-            }
+            for (int q = 0; q < DIM; ++q)
+                if (p > 0 && (p - 1) / 2 == q) xi[0][q] = xi0[q] + sg * r / Real<real>::w(m, q)[c0[q]];
         }
-        rk4<real, DIM, P>(m, v, c, xi, h, substeps, real(-1));
-        out_cell[b] = static_cast<int32_t>(cell_of<DIM>(m, c[0]));
+        rk4<real, DIM, 1>(m, v, c, xi, h, substeps, real(-1));
+        double pos[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) out_xi[3 * b + a] = xi[0][a];
-        double sum = 0.0;
+        for (int q = 0; q < DIM; ++q) pos[q] = position<real>(m, q, c[0][q], xi[0][q]);
+        double cen[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-        for (int p = 1; p < P; ++p) {
+        for (int q = 0; q < DIM; ++q) cen[q] = __shfl_sync(0xffffffffu, pos[q], base < 32 ? base : 0);
+        double dist = 0.0;
+        {
             double d2 = 0.0;
 #pragma unroll
             for (int q = 0; q < DIM; ++q) {
-                const double dq = position<real>(m, q, c[p][q], xi[p][q]) - position<real>(m, q, c[0][q], xi[0][q]);
+                const double dq = pos[q] - cen[q];
                 d2 += dq * dq;
             }
-            sum += sqrt(d2);
+            dist = sqrt(d2);
         }
-        out_rhat[b] = static_cast<real>(sum / (2.0 * DIM));
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 1; q < G; ++q) {
+            const int src = base + q < 32 ? base + q : 0;
+            sum += __shfl_sync(0xffffffffu, dist, src);
+        }
+        if (valid && p == 0) {
+            out_cell[b] = static_cast<int32_t>(cell_of<DIM>(m, c[0]));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out_xi[3 * b + a] = xi[0][a];
+            out_rhat[b] = static_cast<real>(sum / (2.0 * DIM));
+        }
     }
 }
 
@@ -276,12 +294,14 @@ static void track_in(bchar_mesh_t m, real h, int substeps, int32_t *cell, real *
         else
             k_track_centres<real, 3><<<blocks_for(groups, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
                                                                                       cell, xi, rhat);
-    } else if (m->dim == 2) {
-        k_track_balls<real, 2><<<blocks_for(m->nballs, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
-                                                                                   cell, xi, rhat);
-    } else {
-        k_track_balls<real, 3><<<blocks_for(m->nballs, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs,
-                                                                                   cell, xi, rhat);
+    } else if (m->dim == 2) {  // 6 balls per warp
+        const int64_t threads = (m->nballs + 5) / 6 * 32;
+        k_track_balls<real, 2><<<blocks_for(threads, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs, cell,
+                                                                                  xi, rhat);
+    } else {  // 4 balls per warp
+        const int64_t threads = (m->nballs + 3) / 4 * 32;
+        k_track_balls<real, 3><<<blocks_for(threads, 128), 128, 0, m->stream>>>(mv, vv, h, substeps, m->nballs, cell,
+                                                                                  xi, rhat);
     }
     ++m->launches;
 }

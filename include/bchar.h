@@ -64,12 +64,20 @@ typedef struct {
     double cfl;         /* 0.5 */
     double drop_tol;    /* entries V_KM < drop_tol |K|_phi are dropped (1e-12) */
     double penalty;     /* eps of the penalised minimisation (1e-7), see bchar_step */
-    double qp_tol;      /* stop when the L1 optimality residual <= qp_tol * sum |K|_phi (1e-14) */
+    double qp_tol;      /* stop when the L1 optimality residual <= qp_tol * sum |K|_phi (1e-14);
+                           the iterations stop at a floor of about 1e-9..1e-11 (rounding in the
+                           near-null directions of the dual), so a smaller qp_tol ends at the
+                           floor, with qp_converged = 0 in bchar_step_info */
     int qp_max_iter;    /* cap on conjugate-gradient iterations per solve (200000) */
     int qp_max_refine;  /* cap on refinement rounds (60) */
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
     int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
                            1 = aggregation multigrid (default), 0 = Jacobi */
+    int qp_warm_start;  /* 1 (default): start the minimisation from the dual of the handle's
+                           previous step (the rows and columns are the same cells, and the
+                           dual changes little between steps: 30-60 % fewer iterations),
+                           except every 32nd step, which starts from zero; 0: always start
+                           from zero.  The result meets qp_tol either way. */
 } bchar_options;
 
 typedef struct {

@@ -28,7 +28,8 @@ class Options(ctypes.Structure):
     _fields_ = [("balls_per_axis", ctypes.c_int), ("n_scale", ctypes.c_int), ("precision", ctypes.c_int),
                 ("substeps", ctypes.c_int), ("cfl", ctypes.c_double), ("drop_tol", ctypes.c_double),
                 ("penalty", ctypes.c_double), ("qp_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int),
-                ("qp_max_refine", ctypes.c_int), ("div_tol", ctypes.c_double), ("qp_precond", ctypes.c_int)]
+                ("qp_max_refine", ctypes.c_int), ("div_tol", ctypes.c_double), ("qp_precond", ctypes.c_int),
+                ("qp_warm_start", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

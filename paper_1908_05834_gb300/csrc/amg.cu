@@ -315,40 +315,186 @@ __device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
     return cnt;
 }
 
-__global__ void k_coarse_count(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
-                               const int32_t *col, const double *val, const double *exc, const int32_t *agg,
-                               int32_t *rowcnt, int *overflow) {
-    int32_t cbuf[kCoarseCap];
-    double vbuf[kCoarseCap];
-    GRID_STRIDE(I, nco) {
-        double e;
-        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
-        if (c < 0) {
-            atomicOr(overflow, 1);
-            rowcnt[I] = 0;
-        } else {
-            rowcnt[I] = c;
+// The same rows built by one warp per coarse node I: the members' entries are
+// gathered into shared memory in arrival order (members in order, then each
+// member's entries), sorted by (J, arrival), and each run of equal J is summed
+// by one lane in arrival order -- the order in which the insertion above adds
+// them, so the coarse operator is the same bit for bit.  A row with more than
+// kMergeCap raw entries is built by the warp's first lane with coarse_row.
+constexpr int kMergeCap = 512;
+constexpr int kMergeWarps = 4;  // warps per block
+struct MergeSmem {
+    int32_t key[kMergeCap];
+    int32_t pos[kMergeCap];
+    double val[kMergeCap];
+};
+
+// Gathers row I into sm; returns the raw entry count (> kMergeCap: not all
+// gathered) and the coarse excess in *eI (valid in every lane).
+__device__ int gather_row(int64_t I, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr, const int32_t *col,
+                          const double *val, const double *exc, const int32_t *agg, MergeSmem &sm, double *eI) {
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    double e_sum = 0.0;
+    for (int64_t k = mptr[I]; k < mptr[I + 1]; ++k) {
+        const int32_t m = mlist[k];
+        e_sum += exc[m];
+        const int64_t b = ptr[m], e = ptr[m + 1];
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t idx = base + lane;
+            const int32_t J = idx < e ? agg[col[idx]] : -1;
+            const bool keep = idx < e && J != I;
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            const int at = n + __popc(mask & ((1u << lane) - 1u));
+            if (keep && at < kMergeCap) {
+                sm.key[at] = J;
+                sm.pos[at] = at;
+                sm.val[at] = val[idx];
+            }
+            n += __popc(mask);
+        }
+    }
+    *eI = e_sum;
+    __syncwarp();
+    return n;
+}
+
+// Sorts the first n gathered entries by (key, pos) (bitonic, padded to a
+// power of two with keys that sort last).
+__device__ void sort_row(MergeSmem &sm, int n) {
+    const int lane = threadIdx.x & 31;
+    int P = 32;
+    while (P < n) P <<= 1;
+    for (int i = n + lane; i < P; i += 32) {
+        sm.key[i] = 0x7fffffff;
+        sm.pos[i] = 0x7fffffff;
+        sm.val[i] = 0.0;
+    }
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const bool greater = sm.key[i] > sm.key[l] || (sm.key[i] == sm.key[l] && sm.pos[i] > sm.pos[l]);
+                    if (greater == up) {
+                        const int32_t tk = sm.key[i], tp = sm.pos[i];
+                        const double tv = sm.val[i];
+                        sm.key[i] = sm.key[l];
+                        sm.pos[i] = sm.pos[l];
+                        sm.val[i] = sm.val[l];
+                        sm.key[l] = tk;
+                        sm.pos[l] = tp;
+                        sm.val[l] = tv;
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
 }
 
-__global__ void k_coarse_fill(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
-                              const int32_t *col, const double *val, const double *exc, const int32_t *agg,
-                              const int64_t *cptr, int32_t *ccol, double *cval, double *cdiag, double *cexc) {
-    int32_t cbuf[kCoarseCap];
-    double vbuf[kCoarseCap];
-    GRID_STRIDE(I, nco) {
-        double e;
-        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
-        const int64_t dst = cptr[I];
-        double d = e;
-        for (int k = 0; k < c; ++k) {
-            ccol[dst + k] = cbuf[k];
-            cval[dst + k] = vbuf[k];
-            d -= vbuf[k];
+// Runs of equal keys in the sorted entries: calls out(r, key, sum) once per
+// run (r = run index, runs in key order; the sum in arrival order); returns
+// the number of runs.
+template <class F> __device__ int merge_runs(const MergeSmem &sm, int n, F out) {
+    const int lane = threadIdx.x & 31;
+    int runs = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool start = i < n && (i == 0 || sm.key[i] != sm.key[i - 1]);
+        const unsigned mask = __ballot_sync(0xffffffffu, start);
+        if (start) {
+            const int r = runs + __popc(mask & ((1u << lane) - 1u));
+            double sum = sm.val[i];
+            for (int q = i + 1; q < n && sm.key[q] == sm.key[i]; ++q) sum += sm.val[q];
+            out(r, sm.key[i], sum);
         }
-        cdiag[I] = d;
-        cexc[I] = e;
+        runs += __popc(mask);
+    }
+    return runs;
+}
+
+__global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_count(int64_t nco, const int64_t *mptr,
+                                                                   const int32_t *mlist, const int64_t *ptr,
+                                                                   const int32_t *col, const double *val,
+                                                                   const double *exc, const int32_t *agg,
+                                                                   int32_t *rowcnt, int *overflow) {
+    __shared__ MergeSmem sm_all[kMergeWarps];
+    MergeSmem &sm = sm_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kMergeWarps;
+    for (int64_t I = blockIdx.x * static_cast<int64_t>(kMergeWarps) + (threadIdx.x >> 5); I < nco; I += nwarps) {
+        double e;
+        const int n = gather_row(I, mptr, mlist, ptr, col, val, exc, agg, sm, &e);
+        int c;
+        if (n <= kMergeCap) {
+            sort_row(sm, n);
+            c = merge_runs(sm, n, [](int, int32_t, double) {});
+        } else {
+            c = 0;
+            if (lane == 0) {
+                int32_t cbuf[kCoarseCap];
+                double vbuf[kCoarseCap];
+                c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+            }
+            c = __shfl_sync(0xffffffffu, c, 0);
+        }
+        if (lane == 0) {
+            if (c < 0) {
+                atomicOr(overflow, 1);
+                rowcnt[I] = 0;
+            } else {
+                rowcnt[I] = c;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_fill(int64_t nco, const int64_t *mptr,
+                                                                  const int32_t *mlist, const int64_t *ptr,
+                                                                  const int32_t *col, const double *val,
+                                                                  const double *exc, const int32_t *agg,
+                                                                  const int64_t *cptr, int32_t *ccol, double *cval,
+                                                                  double *cdiag, double *cexc) {
+    __shared__ MergeSmem sm_all[kMergeWarps];
+    MergeSmem &sm = sm_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kMergeWarps;
+    for (int64_t I = blockIdx.x * static_cast<int64_t>(kMergeWarps) + (threadIdx.x >> 5); I < nco; I += nwarps) {
+        double e;
+        const int n = gather_row(I, mptr, mlist, ptr, col, val, exc, agg, sm, &e);
+        const int64_t dst = cptr[I];
+        int c;
+        if (n <= kMergeCap) {
+            sort_row(sm, n);
+            c = merge_runs(sm, n, [&](int r, int32_t J, double v) {
+                ccol[dst + r] = J;
+                cval[dst + r] = v;
+            });
+        } else {
+            c = 0;
+            if (lane == 0) {
+                int32_t cbuf[kCoarseCap];
+                double vbuf[kCoarseCap];
+                c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+                for (int k = 0; k < c; ++k) {
+                    ccol[dst + k] = cbuf[k];
+                    cval[dst + k] = vbuf[k];
+                }
+            }
+            c = __shfl_sync(0xffffffffu, c, 0);
+        }
+        __syncwarp();
+        if (lane == 0) {  // the diagonal from the merged entries, in their order
+            double d = e;
+            for (int k = 0; k < c; ++k) d -= cval[dst + k];
+            cdiag[I] = d;
+            cexc[I] = e;
+        }
+        __syncwarp();
     }
 }
 
@@ -611,7 +757,7 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         k_members_sort<<<blocks_for(nco), kThreads, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
         m->launches += 3;
         int32_t *rowcnt = flag;
-        k_coarse_count<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
+        k_coarse_count<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
                                                             ptr<int64_t>(Fr.ptr),
                                                             ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
                                                             ptr<int32_t>(Fr.agg), rowcnt, overflow);
@@ -627,7 +773,7 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
             !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
             return false;
-        k_coarse_fill<<<blocks_for(nco, 128), 128, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
+        k_coarse_fill<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
                                                            ptr<int64_t>(Fr.ptr),
                                                            ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
                                                            ptr<int32_t>(Fr.agg), ptr<int64_t>(C.ptr),

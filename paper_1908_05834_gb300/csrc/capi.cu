@@ -115,7 +115,8 @@ bool options_valid(const bchar_options &o) {
     return o.balls_per_axis >= 1 && o.balls_per_axis <= 8 && o.n_scale >= 0 && o.n_scale <= 100000 &&
            (o.precision == BCHAR_FP64 || o.precision == BCHAR_FP32_SPLIT) && o.substeps >= 0 && o.cfl > 0.0 &&
            o.drop_tol >= 0.0 && o.drop_tol < 1.0 && o.penalty > 0.0 && o.qp_tol > 0.0 && o.qp_max_iter >= 0 &&
-           o.qp_max_refine >= 0 && o.div_tol > 0.0 && (o.qp_precond == 0 || o.qp_precond == 1);
+           o.qp_max_refine >= 0 && o.div_tol > 0.0 && (o.qp_precond == 0 || o.qp_precond == 1) &&
+           (o.qp_warm_start == 0 || o.qp_warm_start == 1);
 }
 
 }  // namespace
@@ -136,6 +137,7 @@ void bchar_default_options(bchar_options *o) {
     o->qp_max_refine = 60;
     o->div_tol = 1e-9;
     o->qp_precond = 1;
+    o->qp_warm_start = 1;
 }
 
 const char *bchar_status_string(bchar_status s) {

@@ -164,6 +164,8 @@ struct bchar_mesh_s {
     int amg_levels = 0;
     int64_t amg_coarsest = 0;
     bool have_step = false;
+    bool have_dual = false;  // qy holds the dual of the last successful minimisation
+    int warm_steps = 0;      // consecutive warm-started minimisations
     int launches = 0;
 };
 

@@ -447,6 +447,16 @@ __global__ void k_cg_pupdate(int64_t n2, const double *z, double *p, const CgSta
     GRID_STRIDE(l, n2) p[l] = z[l] + beta * p[l];
 }
 
+// Warm start: x_e = a_e (y_i + y_{n+j}) from a dual y kept from the
+// previous step (x = A-hat^T y on the new matrix).
+__global__ void k_qp_warm(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aN, const double *y,
+                          double *qx) {
+    GRID_STRIDE(i, nc) {
+        const double yi = y[i];
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) qx[e] = aN[e] * (yi + y[nc + col[e]]);
+    }
+}
+
 // x_e += a_e (d_i + d_{n+j}), y += d
 __global__ void k_qp_accumulate(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aN,
                                 const double *d, double *qx, double *y) {
@@ -473,6 +483,18 @@ static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res,
 #endif
 constexpr double kInnerReduction = BCHAR_INNER_REDUCTION;
 constexpr double kFp32Above = 1e-9;  // relative optimality residual above which the V-cycle runs in FP32
+// A round of the conjugate gradients ends when its residual has not dropped
+// by 1 % for kStallIters iterations; the refinement ends when a round that
+// ended so improved the optimality residual by less than a factor of two.
+// Below a floor of about 1e-9..1e-11 of sum |K|_phi (near-null components of
+// the dual, which the operator hardly sees, accumulate in y) the iterations
+// stop making progress, so a tolerance under that floor ends at the floor
+// instead of at qp_max_iter; qp_converged reports whether qp_tol was met.
+constexpr int kStallIters = 400;
+// The warm start (see bchar_options.qp_warm_start) begins from zero every
+// kWarmResetSteps steps, so that near-null components cannot pile up in the
+// dual over many steps.
+constexpr int kWarmResetSteps = 32;
 
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
@@ -496,8 +518,17 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                                       ptr<double>(m->aN), ptr<double>(m->bloc), ptr<double>(m->volphi), eps, a2,
                                       diag, ptr<double>(m->qexc), rhs);
     k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, ptr<int32_t>(m->csc_src), a2, a2c);
-    cudaMemsetAsync(qx, 0, sizeof(double) * nnz, s);
-    cudaMemsetAsync(y, 0, sizeof(double) * n2, s);
+    if (m->opt.qp_warm_start && m->have_dual && m->warm_steps < kWarmResetSteps) {
+        ++m->warm_steps;
+        k_qp_warm<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                                                     ptr<double>(m->aN), y, qx);
+        ++m->launches;
+    } else {
+        cudaMemsetAsync(qx, 0, sizeof(double) * nnz, s);
+        cudaMemsetAsync(y, 0, sizeof(double) * n2, s);
+        m->warm_steps = 0;
+    }
+    m->have_dual = false;  // set again below once this solve has finished
     m->launches += 2;
     const bool amg = m->opt.qp_precond == 1 && amg_build(m, m->amg);
     const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: residual history on stderr
@@ -514,7 +545,8 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
     bool exec_fp32 = true;
     int graph_launches = 0;
     const double target_abs = m->opt.qp_tol * total_volphi(m);
-    double kkt = 0.0;
+    double kkt = 0.0, prev_kkt = INFINITY;
+    bool stalled = false;
     for (rounds = 0; rounds <= m->opt.qp_max_refine; ++rounds) {
         k_qp_kkt<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
                                         ptr<int32_t>(m->csc_src), ptr<double>(m->aN), qx, y, rhs,
@@ -525,6 +557,8 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         cudaStreamSynchronize(s);
         if (trace) fprintf(stderr, "[bchar] round %d kkt_l1 %.3e (target %.3e)\n", rounds, kkt, target_abs);
         if (kkt <= target_abs || rounds == m->opt.qp_max_refine || iters >= m->opt.qp_max_iter) break;
+        if (stalled && kkt > 0.5 * prev_kkt) break;  // the floor: rounds no longer improve
+        prev_kkt = kkt;
         // restart the conjugate gradients from the true residual once it has
         // dropped by kInnerReduction: on these ill-conditioned systems short
         // cycles lose less to round-off than one long one
@@ -592,6 +626,9 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
             m->launches = before;
         }
         int done = 0;
+        double best = INFINITY;
+        int best_at = 0;
+        stalled = false;
         while (!done) {
             if (exec) {
                 cudaGraphLaunch(exec, s);
@@ -605,6 +642,13 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                 fprintf(stderr, "[bchar] round %d iter %d res_l1 %.3e target %.3e\n", rounds, host_st->iters,
                         host_st->res_l1, host_st->target);
             if (host_st->converged || iters + host_st->iters >= m->opt.qp_max_iter) done = 1;
+            if (host_st->res_l1 < 0.99 * best) {
+                best = host_st->res_l1;
+                best_at = host_st->iters;
+            } else if (host_st->iters - best_at >= kStallIters) {
+                stalled = true;
+                done = 1;
+            }
         }
         iters += host_st->iters;
         k_qp_accumulate<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
@@ -612,6 +656,7 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         ++m->launches;
     }
     if (exec) cudaGraphExecDestroy(exec);
+    m->have_dual = isfinite(kkt);
     *cg_iters = iters;
     *refines = rounds;
     m->amg_levels = amg ? m->amg.nlev : 0;

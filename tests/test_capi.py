@@ -36,5 +36,29 @@ def test_binding_marshals_options_and_status_strings():
     o = bchar.default_options()
     assert (o.balls_per_axis, o.n_scale, o.precision) == (2, 10, bchar.FP64)
     assert o.penalty == pytest.approx(1e-7) and o.qp_tol == pytest.approx(1e-14)
+    # the last fields: a mismatch between the ctypes mirror and the header would show here
+    assert (o.qp_precond, o.qp_warm_start) == (1, 1)
     assert bchar.bchar_status_string(0) == b"ok"
     assert b"boundary" in bchar.bchar_status_string(4)
+
+
+def test_footprint_estimate_on_the_host():
+    """bchar_estimate_device_bytes needs no GPU: it grows with the mesh, counts
+    the tight ball packing of stretched cells, and rejects bad arguments."""
+    from paper_1908_05834_gb300 import build
+    build.build()
+    import numpy as np
+    from paper_1908_05834_gb300 import bchar, inputs
+    u = [inputs.uniform_coords(64)] * 2
+    e64 = bchar.estimate_device_bytes(u)
+    e128 = bchar.estimate_device_bytes([inputs.uniform_coords(128)] * 2)
+    assert 3.5 < e128 / e64 < 4.5  # ~ proportional to the cells
+    rng = np.random.Generator(np.random.PCG64(1))
+    s = [inputs.stretched_coords(rng, 64, 0.5, 1.5), inputs.stretched_coords(rng, 64, 0.5, 1.5)]
+    assert bchar.estimate_device_bytes(s) > e64  # stretched cells hold more balls
+    e3 = bchar.estimate_device_bytes([inputs.uniform_coords(16)] * 3)
+    assert e3 > 16 ** 3 * 1000
+    with pytest.raises(bchar.BcharError):
+        bchar.estimate_device_bytes(u, bchar.default_options(qp_warm_start=2))
+    with pytest.raises(bchar.BcharError):
+        bchar.estimate_device_bytes([np.array([0.0, 0.5, 0.5, 1.0])] * 2)  # a zero width

@@ -153,6 +153,52 @@ def test_vortex32_full_run_fp64(bc):
     mesh.close()
 
 
+def test_warm_start_fewer_iterations_same_result(bc):
+    """Starting the minimisation from the previous step's dual changes only
+    the iterations it takes: both runs meet the tolerance and agree."""
+    import torch
+    wl = inputs.workload("vortex2d_1024", n=48)
+    runs = {}
+    for warm in (0, 1):
+        o = bc.default_options(precision=bc.FP32_SPLIT, qp_tol=1e-6, qp_warm_start=warm)
+        mesh = bc.Mesh(wl.coords, wl.phi, o)
+        c = torch.tensor(wl.c0, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(c)
+        iters = []
+        for st in range(6):
+            mesh.set_velocity(wl.faces(st))
+            info = mesh.step(wl.dt, c, out)
+            c, out = out, c
+            iters.append(info["cg_iters"])
+            assert info["kkt_rel"] <= 1e-6 and info["qp_converged"]
+        runs[warm] = (c.cpu().numpy(), iters)
+        mesh.close()
+    (c0, it0), (c1, it1) = runs[0], runs[1]
+    assert it1[0] == it0[0]  # the first step has no previous dual
+    assert sum(it1[1:]) < sum(it0[1:]), (it0, it1)
+    assert np.abs(c1 - c0).sum() / np.abs(c0).sum() <= 1e-5
+
+
+def test_tolerance_below_the_floor_ends_at_the_floor(bc):
+    """A tolerance the iterations cannot reach (rounding in the near-null
+    directions of the dual) ends at the floor within a bounded number of
+    iterations, reports qp_converged = 0, and still conserves mass."""
+    import torch
+    wl = inputs.workload("vortex2d_1024", n=48)
+    o = bc.default_options(precision=bc.FP32_SPLIT, qp_tol=1e-14, qp_warm_start=0)
+    mesh = bc.Mesh(wl.coords, wl.phi, o)
+    c = torch.tensor(wl.c0, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(c)
+    for st in range(3):
+        mesh.set_velocity(wl.faces(st))
+        info = mesh.step(wl.dt, c, out)
+        c, out = out, c
+        assert info["cg_iters"] < 50000, info["cg_iters"]
+        assert info["kkt_rel"] <= 1e-7
+        assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    mesh.close()
+
+
 @pytest.mark.parametrize("name", ["stretched2d", "porous3d"])
 def test_fp32_split_error_budget(bc, name):
     wl = _case(name)

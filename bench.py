@@ -205,9 +205,14 @@ def run_ours(args, rank, world, local_rank):
     sm_bytes = algorithmic_bytes("smooth", nc, last["nnz"])
     achieved = sm_bytes / (stage_ms["smooth"] * 1e-3) / 1e9
     mv_bytes = algorithmic_bytes("cg_matvec", nc, last["nnz"])
+    # DRAM bytes of one finest-level sweep from an ncu capture of the same kernel
+    # on the 512x512 case of this recipe (profiles/k_jacobi_vortex2d_512.md:
+    # 23.92 MB read, no write reaching DRAM), scaled by cells to this launch
+    traffic = round(23.921408e6 / (512 * 512) * nc) if args.workload == WORKLOAD else None
     roofline = {"bound": "hbm", "kernel": "k_jacobi<float> (finest multigrid level, post-smoothing)",
                 "achieved": round(achieved, 1),
-                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "traffic_note": "dram read+write per launch, ncu capture at 512x512 scaled by cells" if traffic else None,
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": sm_bytes,
                 "mean_launch_ms": round(stage_ms["smooth"], 5),
                 "k_cg_matvec": {"achieved": round(mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9, 1),

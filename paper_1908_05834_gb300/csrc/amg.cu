@@ -293,7 +293,7 @@ __device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
         e_sum += exc[m];
         for (int64_t e = ptr[m]; e < ptr[m + 1]; ++e) {
             const int32_t J = agg[col[e]];
-            if (J == I) continue;
+            if (J == I || J < 0) continue;  // internal edge, or a neighbour without coarse counterpart
             // insertion into the sorted buffer, merging equal columns
             int pos = cnt;
             while (pos > 0 && cbuf[pos - 1] > J) --pos;
@@ -343,7 +343,7 @@ __device__ int gather_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
         for (int64_t base = b; base < e; base += 32) {
             const int64_t idx = base + lane;
             const int32_t J = idx < e ? agg[col[idx]] : -1;
-            const bool keep = idx < e && J != I;
+            const bool keep = idx < e && J != I && J >= 0;
             const unsigned mask = __ballot_sync(0xffffffffu, keep);
             const int at = n + __popc(mask & ((1u << lane) - 1u));
             if (keep && at < kMergeCap) {
@@ -611,7 +611,8 @@ __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *c
         T s = diag[i] * xi;
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t j = col[e];
-            s += val[e] * (x[j] + xc[agg[j]]);
+            const int32_t J = agg[j];  // < 0 only with aggregates kept from an earlier matrix
+            s += val[e] * (J >= 0 ? x[j] + xc[J] : x[j]);
         }
         const T om = static_cast<T>(e1 == e0 ? 1.0 : kOmega);
         x_out[i] = xi + om * (b[i] - s) / diag[i];
@@ -675,10 +676,70 @@ static bool level_vectors(bchar_mesh_t m, AmgLevel &L) {
            ensure(m, L.b, sizeof(double) * L.n) && ensure(m, L.r, sizeof(double) * L.n);
 }
 
-bool amg_build(bchar_mesh_t m, Amg &amg) {
+// The operators of levels 1..nlev-1 from level 0, on the kept aggregates.
+// Returns false when a coarse row overflows (then the caller rebuilds).
+static bool amg_reoperate(bchar_mesh_t m, Amg &amg, bool &overflowed) {
+    cudaStream_t s = m->stream;
+    overflowed = false;
+    for (int l = 0; l + 1 < amg.nlev; ++l) {
+        AmgLevel &F = amg.levels[l];
+        AmgLevel &C = amg.levels[l + 1];
+        const double *fexc = F.exc_ext ? F.exc_ext : ptr<double>(F.exc);
+        const int64_t nco = C.n;
+        if (!ensure(m, amg.tmp, sizeof(int32_t) * (nco + 1) + 64)) return false;
+        int32_t *rowcnt = ptr<int32_t>(amg.tmp);
+        int *overflow = reinterpret_cast<int *>(rowcnt + nco + 1);
+        cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        k_coarse_count<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
+            nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(F.ptr), ptr<int32_t>(F.col),
+            ptr<double>(F.val), fexc, ptr<int32_t>(F.agg), rowcnt, overflow);
+        scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
+        int64_t cnnz = 0;
+        int ovf = 0;
+        cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + nco, sizeof cnnz, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&ovf, overflow, sizeof ovf, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        m->launches += 2;
+        if (ovf) {
+            overflowed = true;
+            return true;
+        }
+        C.nnz = cnnz;
+        if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
+            !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
+            return false;
+        k_coarse_fill<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
+            nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(F.ptr), ptr<int32_t>(F.col),
+            ptr<double>(F.val), fexc, ptr<int32_t>(F.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
+            ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
+        ++m->launches;
+    }
+    return true;
+}
+
+static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg);
+
+bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
     cudaStream_t s = m->stream;
     const int64_t nc = m->nc, nnz = m->nnz;
     if (amg.levels.empty()) amg.levels.resize(1);
+    if (reuse && amg.nlev > 1 && amg.levels[0].n == 2 * nc) {
+        AmgLevel &L0 = amg.levels[0];
+        L0.nnz = 2 * nnz;
+        if (!ensure(m, L0.col, sizeof(int32_t) * L0.nnz) || !ensure(m, L0.val, sizeof(double) * L0.nnz)) return false;
+        k_level0_ptr<<<blocks_for(L0.n + 1), kThreads, 0, s>>>(nc, nnz, ptr<int64_t>(m->row_ptr),
+                                                               ptr<int64_t>(m->col_ptr), ptr<int64_t>(L0.ptr));
+        k_level0_fill<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                                                            ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
+                                                            ptr<double>(m->a2), ptr<double>(m->a2c),
+                                                            ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
+                                                            ptr<double>(L0.val));
+        m->launches += 2;
+        bool overflowed = false;
+        if (!amg_reoperate(m, amg, overflowed)) return false;
+        if (!overflowed) return amg_scaled_copies(m, amg);
+        // a coarse row of the kept hierarchy overflows on this matrix: build anew
+    }
     amg.nlev = 1;
     AmgLevel &L0 = amg.levels[0];
     L0.n = 2 * nc;
@@ -782,6 +843,12 @@ bool amg_build(bchar_mesh_t m, Amg &amg) {
         ++m->launches;
         ++amg.nlev;
     }
+    return amg_scaled_copies(m, amg);
+}
+
+// FP32 and FP64 copies of every level's operator, divided by a fixed scale.
+static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg) {
+    cudaStream_t s = m->stream;
     // FP32 copies of every level, divided by the square of the largest |K|_phi
     amg.scale = m->max_volphi * m->max_volphi;
     const double inv = 1.0 / amg.scale;

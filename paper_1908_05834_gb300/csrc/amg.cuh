@@ -5,7 +5,11 @@
 
 namespace bchar {
 
-bool amg_build(bchar_mesh_t m, Amg &amg);
+// Builds the hierarchy for the current matrix.  With reuse, the aggregates of
+// the hierarchy already built (on an earlier matrix of the same handle) are
+// kept and only the level operators are recomputed from the new matrix; a
+// node that has no coarse counterpart then simply gets no coarse correction.
+bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse = false);
 // z = M^-1 res (one V-cycle in FP32 or FP64).  With b_ready the caller has
 // already written the sign-flipped res into the finest level's right-hand side
 // in that precision.  With rp, pa, pb the last kernel also writes per-block

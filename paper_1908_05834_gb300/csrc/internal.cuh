@@ -166,6 +166,9 @@ struct bchar_mesh_s {
     bool have_step = false;
     bool have_dual = false;  // qy holds the dual of the last successful minimisation
     int warm_steps = 0;      // consecutive warm-started minimisations
+    int amg_age = -1;        // steps since the multigrid aggregation was built (-1: none yet)
+    int amg_built_iters = 0; // CG iterations of the solve right after that build
+    int last_cg_iters = 0;   // CG iterations of the previous solve
     int launches = 0;
 };
 

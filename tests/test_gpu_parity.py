@@ -179,6 +179,30 @@ def test_warm_start_fewer_iterations_same_result(bc):
     assert np.abs(c1 - c0).sum() / np.abs(c0).sum() <= 1e-5
 
 
+def test_porous3d_steps_with_kept_aggregation_match_oracle(bc):
+    """Consecutive 3D steps on one handle: from the second step on, the
+    multigrid keeps its aggregation and the minimisation starts from the
+    previous dual; every step still matches the oracle."""
+    import torch
+    wl = _case("porous3d")
+    om = oracle.Mesh(wl.coords, wl.phi)
+    mesh = bc.Mesh(wl.coords, wl.phi, bc.default_options())
+    c_ref = wl.c0.astype(np.float64)
+    c_gpu = torch.tensor(c_ref, device="cuda")
+    out = torch.empty_like(c_gpu)
+    m0 = oracle.total_mass(om, c_ref)
+    for st in range(3):
+        faces = wl.faces(st)
+        mesh.set_velocity(faces)
+        info = mesh.step(wl.dt, c_gpu, out)
+        c_gpu, out = out, c_gpu
+        c_ref = oracle.step(om, faces, wl.dt, c_ref)["c"]
+        g = c_gpu.cpu().numpy()
+        assert np.abs(g - c_ref).sum() / np.abs(c_ref).sum() <= 1e-5, st
+        assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * m0
+    mesh.close()
+
+
 def test_tolerance_below_the_floor_ends_at_the_floor(bc):
     """A tolerance the iterations cannot reach (rounding in the near-null
     directions of the dual) ends at the floor within a bounded number of

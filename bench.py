@@ -34,6 +34,23 @@ WORKLOAD = "vortex2d_1024"
 ORACLE_SAMPLE_N = 128  # cells per axis of the oracle's bounded sample (same recipe)
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself without one):
+    the whole job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Cell-steps per second of the whole job: every rank steps its own replica."""
+    return cells_per_rank * steps * world / seconds
+
+
 def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -172,13 +189,8 @@ def run_ours(args, rank, world, local_rank):
         times.append(e0.elapsed_time(e1) / 1e3)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = nc * args.steps * world / total
+    total = max_over_ranks(sum(times), dev)
+    value = whole_job_rate(nc, args.steps, world, total)
 
     # dominant kernel: live CUDA-event timing of the stages on the last step's data
     last = infos[-1]

@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <time.h>
 
 #include "amg.cuh"
 #include "device.cuh"
@@ -506,7 +507,20 @@ constexpr int kWarmResetSteps = 32;
 // matching costs a few ms.
 constexpr int kAmgReuseSteps = 8;
 
+// Host wall clock in milliseconds (for the diagnostic trace only).
+static double trace_ms() {
+    timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return t.tv_sec * 1e3 + t.tv_nsec * 1e-6;
+}
+
 void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
+    const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: residual history and phases on stderr
+    double t_start = 0.0, t_setup = 0.0, t_graph = 0.0;
+    if (trace) {
+        cudaStreamSynchronize(m->stream);
+        t_start = trace_ms();
+    }
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
     const int bl = blocks_for(n2);
     const double eps = m->opt.penalty;
@@ -544,7 +558,11 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
                        m->last_cg_iters <= 1.5 * m->amg_built_iters + 5;
     const bool amg = m->opt.qp_precond == 1 && amg_build(m, m->amg, reuse);
     m->amg_age = !amg ? -1 : (reuse ? m->amg_age + 1 : 0);
-    const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: residual history on stderr
+    if (trace) {
+        cudaStreamSynchronize(m->stream);
+        t_setup = trace_ms();
+        fprintf(stderr, "[bchar] set-up and multigrid %.3f ms (%s)\n", t_setup - t_start, reuse ? "kept aggregates" : "built");
+    }
     if (trace && amg) {
         fprintf(stderr, "[bchar] multigrid levels:");
         for (int l = 0; l < m->amg.nlev; ++l)
@@ -622,6 +640,7 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
             }
         };
         if (!exec) {
+            const double t0 = trace ? trace_ms() : 0.0;
             const int before = m->launches;
             cudaGraph_t graph = nullptr;
             bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -637,6 +656,7 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
             }
             graph_launches = m->launches - before;
             m->launches = before;
+            if (trace) t_graph += trace_ms() - t0;
         }
         int done = 0;
         double best = INFINITY;
@@ -669,6 +689,11 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         ++m->launches;
     }
     if (exec) cudaGraphExecDestroy(exec);
+    if (trace) {
+        cudaStreamSynchronize(m->stream);
+        fprintf(stderr, "[bchar] capture+instantiate %.3f ms, total %.3f ms, %d iterations\n", t_graph,
+                trace_ms() - t_start, iters);
+    }
     m->have_dual = isfinite(kkt);
     if (m->amg_age == 0) m->amg_built_iters = iters;
     m->last_cg_iters = iters;

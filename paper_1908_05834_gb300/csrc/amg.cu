@@ -109,9 +109,11 @@ __device__ __forceinline__ uint32_t edge_hash(int64_t i, int64_t j) {
 }
 
 // Is neighbour j (weight w > 0) ranked above the current best (class bc, hash bh, index b)?
+// The class is the exponent field of w's bits (monotone in w, read without
+// the FP64 pipe).
 __device__ __forceinline__ bool ranks_above(int64_t i, int32_t j, double w, int32_t b, int bc, uint32_t bh, int &cls,
                                             uint32_t &hs) {
-    cls = ilogb(w);
+    cls = static_cast<int>((__double_as_longlong(w) >> 52) & 0x7ff);
     hs = edge_hash(i, j);
     return b < 0 || cls > bc || (cls == bc && (hs > bh || (hs == bh && j < b)));
 }
@@ -132,7 +134,8 @@ __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, co
                 if (j == i) continue;
                 if (only_free && partner[j] >= 0) continue;
                 const double w = -val[e];
-                if (!(w > 0.0) || !(w >= kStrength * sqrt(di * diag[j]))) continue;
+                // strong: w >= kStrength sqrt(d_i d_j), compared squared (no FP64 square root)
+                if (!(w > 0.0) || !(w * w >= (kStrength * kStrength) * (di * diag[j]))) continue;
                 int cls;
                 uint32_t hs;
                 if (ranks_above(i, j, w, b, bc, bh, cls, hs)) {
@@ -429,7 +432,9 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_count(int64_t nco, 
         double e;
         const int n = gather_row(I, mptr, mlist, ptr, col, val, exc, agg, sm, &e);
         int c;
-        if (n <= kMergeCap) {
+        if (n == 0) {
+            c = 0;
+        } else if (n <= kMergeCap) {
             sort_row(sm, n);
             c = merge_runs(sm, n, [](int, int32_t, double) {});
         } else {
@@ -791,45 +796,47 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         // per-level x buffer as int64 scratch (it holds n + 1 entries)
         int64_t *pos = reinterpret_cast<int64_t *>(ptr<double>(F.x));
         scan_i32_to_i64(m, flag, pos, F.n);
-        int64_t nco = 0;
-        int niso = 0;
-        cudaMemcpyAsync(&nco, pos + F.n, sizeof nco, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&niso, isolated, sizeof niso, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-        const int64_t active = F.n - niso;  // nodes that would have a coarse counterpart
-        if (active <= kCoarsest || nco >= active * kStall || nco < 1) break;  // this is the coarsest level
+        // The coarse level is laid out for U = F.n coarse nodes, a bound on their
+        // number nco, so that its members and row counts are formed before nco is
+        // read back: nodes nco..U-1 have no members and empty rows.  One read-back
+        // per level then returns nco, the isolated nodes and the coarse entries.
         if (static_cast<int>(amg.levels.size()) <= amg.nlev) amg.levels.resize(amg.nlev + 1);
         AmgLevel &Fr = amg.levels[amg.nlev - 1];  // re-fetch after resize
         AmgLevel &C = amg.levels[amg.nlev];
-        C.n = nco;
+        const int64_t U = Fr.n;
+        C.n = U;
         C.diag_ext = nullptr;
         C.exc_ext = nullptr;
-        if (!ensure(m, C.mptr, sizeof(int64_t) * (nco + 1)) || !ensure(m, C.mlist, sizeof(int32_t) * Fr.n) ||
-            !ensure(m, C.ptr, sizeof(int64_t) * (nco + 1)) || !ensure(m, C.diag, sizeof(double) * nco) ||
-            !ensure(m, C.exc, sizeof(double) * nco) || !level_vectors(m, C))
+        if (!ensure(m, C.mptr, sizeof(int64_t) * (U + 1)) || !ensure(m, C.mlist, sizeof(int32_t) * Fr.n) ||
+            !ensure(m, C.ptr, sizeof(int64_t) * (U + 1)) || !ensure(m, C.diag, sizeof(double) * U) ||
+            !ensure(m, C.exc, sizeof(double) * U) || !level_vectors(m, C))
             return false;
         // aggregates: map, member counts -> pointers, members sorted by node
-        cudaMemsetAsync(flag, 0, sizeof(int32_t) * nco, s);
+        cudaMemsetAsync(flag, 0, sizeof(int32_t) * U, s);
         k_aggregates<<<bl, kThreads, 0, s>>>(Fr.n, leader, pos, ptr<int32_t>(Fr.agg), flag);
-        scan_i32_to_i64(m, flag, ptr<int64_t>(C.mptr), nco);
-        cudaMemsetAsync(flag, 0, sizeof(int32_t) * nco, s);
+        scan_i32_to_i64(m, flag, ptr<int64_t>(C.mptr), U);
+        cudaMemsetAsync(flag, 0, sizeof(int32_t) * U, s);
         k_members_fill<<<bl, kThreads, 0, s>>>(Fr.n, ptr<int32_t>(Fr.agg), ptr<int64_t>(C.mptr), flag,
                                                ptr<int32_t>(C.mlist));
-        k_members_sort<<<blocks_for(nco), kThreads, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
+        k_members_sort<<<blocks_for(U), kThreads, 0, s>>>(U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
         m->launches += 3;
         int32_t *rowcnt = flag;
-        k_coarse_count<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
-                                                            ptr<int64_t>(Fr.ptr),
-                                                            ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
-                                                            ptr<int32_t>(Fr.agg), rowcnt, overflow);
-        scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
-        int64_t cnnz = 0;
-        int ovf = 0;
-        cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + nco, sizeof cnnz, cudaMemcpyDeviceToHost, s);
+        k_coarse_count<<<blocks_for(U * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
+            U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fr.ptr), ptr<int32_t>(Fr.col),
+            ptr<double>(Fr.val), fexc, ptr<int32_t>(Fr.agg), rowcnt, overflow);
+        scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), U);
+        int64_t nco = 0, cnnz = 0;
+        int niso = 0, ovf = 0;
+        cudaMemcpyAsync(&nco, pos + Fr.n, sizeof nco, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&niso, isolated, sizeof niso, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + U, sizeof cnnz, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&ovf, overflow, sizeof ovf, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-        m->launches += 3;
+        m->launches += 1;
+        const int64_t active = Fr.n - niso;  // nodes that would have a coarse counterpart
+        if (active <= kCoarsest || nco >= active * kStall || nco < 1) break;  // Fr is the coarsest level
         if (ovf) break;  // a coarse row would be too wide: stop at the finer level
+        C.n = nco;
         C.nnz = cnnz;
         if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
             !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))

@@ -318,6 +318,44 @@ __device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
     return cnt;
 }
 
+// Short coarse rows (2D): one thread per coarse node, merging by insertion.
+__global__ void k_coarse_count_thread(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
+                                      const int32_t *col, const double *val, const double *exc, const int32_t *agg,
+                                      int32_t *rowcnt, int *overflow) {
+    int32_t cbuf[kCoarseCap];
+    double vbuf[kCoarseCap];
+    GRID_STRIDE(I, nco) {
+        double e;
+        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        if (c < 0) {
+            atomicOr(overflow, 1);
+            rowcnt[I] = 0;
+        } else {
+            rowcnt[I] = c;
+        }
+    }
+}
+
+__global__ void k_coarse_fill_thread(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
+                                     const int32_t *col, const double *val, const double *exc, const int32_t *agg,
+                                     const int64_t *cptr, int32_t *ccol, double *cval, double *cdiag, double *cexc) {
+    int32_t cbuf[kCoarseCap];
+    double vbuf[kCoarseCap];
+    GRID_STRIDE(I, nco) {
+        double e;
+        const int c = coarse_row(I, mptr, mlist, ptr, col, val, exc, agg, cbuf, vbuf, &e);
+        const int64_t dst = cptr[I];
+        double d = e;
+        for (int k = 0; k < c; ++k) {
+            ccol[dst + k] = cbuf[k];
+            cval[dst + k] = vbuf[k];
+            d -= vbuf[k];
+        }
+        cdiag[I] = d;
+        cexc[I] = e;
+    }
+}
+
 // The same rows built by one warp per coarse node I: the members' entries are
 // gathered into shared memory in arrival order (members in order, then each
 // member's entries), sorted by (J, arrival), and each run of equal J is summed
@@ -501,6 +539,41 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_fill(int64_t nco, c
         }
         __syncwarp();
     }
+}
+
+// The coarse operator of one level: warp per row where the finer level's rows
+// are wide (the per-thread insertion then works in local memory), thread per
+// row where they are short (a warp's sort would cost more than the merge).
+static bool wide_rows(const AmgLevel &F) { return F.nnz > 8 * F.n; }
+
+static void coarse_count(bchar_mesh_t m, const AmgLevel &F, const AmgLevel &C, int64_t ncoarse, const double *fexc,
+                         int32_t *rowcnt, int *overflow) {
+    AmgLevel &Fm = const_cast<AmgLevel &>(F);
+    AmgLevel &Cm = const_cast<AmgLevel &>(C);
+    if (wide_rows(F))
+        k_coarse_count<<<blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, m->stream>>>(
+            ncoarse, ptr<int64_t>(Cm.mptr), ptr<int32_t>(Cm.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
+            ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), rowcnt, overflow);
+    else
+        k_coarse_count_thread<<<blocks_for(ncoarse, 128), 128, 0, m->stream>>>(
+            ncoarse, ptr<int64_t>(Cm.mptr), ptr<int32_t>(Cm.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
+            ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), rowcnt, overflow);
+    ++m->launches;
+}
+
+static void coarse_fill(bchar_mesh_t m, const AmgLevel &F, AmgLevel &C, int64_t ncoarse, const double *fexc) {
+    AmgLevel &Fm = const_cast<AmgLevel &>(F);
+    if (wide_rows(F))
+        k_coarse_fill<<<blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, m->stream>>>(
+            ncoarse, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
+            ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
+            ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
+    else
+        k_coarse_fill_thread<<<blocks_for(ncoarse, 128), 128, 0, m->stream>>>(
+            ncoarse, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
+            ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
+            ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
+    ++m->launches;
 }
 
 // ---------------------------------------------------------------- V-cycle kernels
@@ -695,16 +768,14 @@ static bool amg_reoperate(bchar_mesh_t m, Amg &amg, bool &overflowed) {
         int32_t *rowcnt = ptr<int32_t>(amg.tmp);
         int *overflow = reinterpret_cast<int *>(rowcnt + nco + 1);
         cudaMemsetAsync(overflow, 0, sizeof(int), s);
-        k_coarse_count<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
-            nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(F.ptr), ptr<int32_t>(F.col),
-            ptr<double>(F.val), fexc, ptr<int32_t>(F.agg), rowcnt, overflow);
+        coarse_count(m, F, C, nco, fexc, rowcnt, overflow);
         scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
         int64_t cnnz = 0;
         int ovf = 0;
         cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + nco, sizeof cnnz, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&ovf, overflow, sizeof ovf, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-        m->launches += 2;
+        ++m->launches;
         if (ovf) {
             overflowed = true;
             return true;
@@ -713,11 +784,7 @@ static bool amg_reoperate(bchar_mesh_t m, Amg &amg, bool &overflowed) {
         if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
             !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
             return false;
-        k_coarse_fill<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
-            nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(F.ptr), ptr<int32_t>(F.col),
-            ptr<double>(F.val), fexc, ptr<int32_t>(F.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
-            ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
-        ++m->launches;
+        coarse_fill(m, F, C, nco, fexc);
     }
     return true;
 }
@@ -821,9 +888,7 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         k_members_sort<<<blocks_for(U), kThreads, 0, s>>>(U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
         m->launches += 3;
         int32_t *rowcnt = flag;
-        k_coarse_count<<<blocks_for(U * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(
-            U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fr.ptr), ptr<int32_t>(Fr.col),
-            ptr<double>(Fr.val), fexc, ptr<int32_t>(Fr.agg), rowcnt, overflow);
+        coarse_count(m, Fr, C, U, fexc, rowcnt, overflow);
         scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), U);
         int64_t nco = 0, cnnz = 0;
         int niso = 0, ovf = 0;
@@ -841,13 +906,7 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
             !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
             return false;
-        k_coarse_fill<<<blocks_for(nco * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, s>>>(nco, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist),
-                                                           ptr<int64_t>(Fr.ptr),
-                                                           ptr<int32_t>(Fr.col), ptr<double>(Fr.val), fexc,
-                                                           ptr<int32_t>(Fr.agg), ptr<int64_t>(C.ptr),
-                                                           ptr<int32_t>(C.col), ptr<double>(C.val),
-                                                           ptr<double>(C.diag), ptr<double>(C.exc));
-        ++m->launches;
+        coarse_fill(m, Fr, C, nco, fexc);
         ++amg.nlev;
     }
     return amg_scaled_copies(m, amg);

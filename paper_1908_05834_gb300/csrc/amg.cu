@@ -590,12 +590,14 @@ template <class T> __global__ void k_scaled_copy(int64_t n, const double *in, T 
 
 // b = S res (S: +1 rows, -1 columns), in the V-cycle's precision
 template <class T> __global__ void k_flip_in(int64_t nc, const double *res, T *b, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(l, 2 * nc) b[l] = static_cast<T>(l < nc ? res[l] : -res[l]);
 }
 
 // z = S x / scale, in FP64
 template <class T> __global__ void k_flip_out(int64_t nc, const T *x, double inv_scale, double *z, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(l, 2 * nc) {
         const double v = static_cast<double>(x[l]) * inv_scale;
@@ -608,6 +610,7 @@ template <class T> __global__ void k_flip_out(int64_t nc, const T *x, double inv
 template <class T>
 __global__ void k_flip_out_dots(int64_t nc, const T *x, double inv_scale, double *z, const double *res,
                                 const double *rp, double *pa, double *pb, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     double a = 0.0, b = 0.0;
     GRID_STRIDE(l, 2 * nc) {
@@ -634,6 +637,7 @@ __device__ __forceinline__ double row_weight(const int64_t *ptr, int64_t i) {
 // x = omega_i b / diag
 template <class T>
 __global__ void k_jacobi0(int64_t n, const int64_t *ptr, const T *diag, const T *b, T *x, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
 }
@@ -642,6 +646,7 @@ __global__ void k_jacobi0(int64_t n, const int64_t *ptr, const T *diag, const T 
 template <class T>
 __global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
                          const T *b, T *x_out, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int64_t e0 = ptr[i], e1 = ptr[i + 1];
@@ -658,6 +663,7 @@ __global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, cons
 template <class T>
 __global__ void k_presmooth_residual(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
                                      const T *b, T *x, T *r, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int64_t e0 = ptr[i], e1 = ptr[i + 1];
@@ -681,6 +687,7 @@ template <class T>
 __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
                                  const int32_t *agg, const T *xc, const T *x, const T *b, T *x_out,
                                  const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int64_t e0 = ptr[i], e1 = ptr[i + 1];
@@ -700,6 +707,7 @@ __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *c
 template <class T>
 __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlist, const T *r, T *bc,
                            const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(I, nco) {
         T s = 0;
@@ -709,6 +717,7 @@ __global__ void k_restrict(int64_t nco, const int64_t *mptr, const int32_t *mlis
 }
 
 template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, const T *xc, T *x, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int32_t I = agg[i];
@@ -721,6 +730,7 @@ template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, cons
 template <class T>
 __global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *b,
                            T *x, T *x2, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
     __syncthreads();
@@ -967,30 +977,30 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
     const int64_t nc = m->nc;
     AmgLevel &L0 = amg.levels[0];
     if (!b_ready) {
-        k_flip_in<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, res, B::b(L0), st);
+        launch_dep(k_flip_in<T>, blocks_for(L0.n), kThreads, s, nc, res, B::b(L0), st);
         ++m->launches;
     }
     for (int l = 0; l < amg.nlev - 1; ++l) {  // down: pre-smooth from zero, residual, restrict
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
-        k_presmooth_residual<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+        launch_dep(k_presmooth_residual<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
                                                         B::diag(L), B::b(L), B::x(L), B::r(L), st);
-        k_restrict<T><<<blocks_for(C.n), kThreads, 0, s>>>(C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
+        launch_dep(k_restrict<T>, blocks_for(C.n), kThreads, s, C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
                                                            B::b(C), st);
         m->launches += 2;
     }
     {  // coarsest: Jacobi sweeps from zero (an even number, so the result is in x)
         AmgLevel &L = amg.levels[amg.nlev - 1];
         if (L.n <= kOneBlock) {
-            k_coarsest<T><<<1, 1024, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
+            launch_dep(k_coarsest<T>, 1, 1024, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
                                              B::b(L), B::x(L), B::x2(L), st);
             ++m->launches;
         } else {
             const int bl = blocks_for(L.n);
-            k_jacobi0<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
+            launch_dep(k_jacobi0<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
             for (int k = 0; k < kLargeCoarsestSweeps; ++k)
-                k_jacobi<T><<<bl, kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+                launch_dep(k_jacobi<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
                                                     B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
                                                     k & 1 ? B::x(L) : B::x2(L), st);
             m->launches += 1 + kLargeCoarsestSweeps;
@@ -1002,22 +1012,22 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
         AmgLevel &C = amg.levels[l + 1];
         const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);
         if (L.n < kFuseBelow) {  // launch-bound levels: one kernel
-            k_prolong_smooth<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+            launch_dep(k_prolong_smooth<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
                                                                      B::val(L), B::diag(L), ptr<int32_t>(L.agg), xc,
                                                                      B::x(L), B::b(L), B::x2(L), st);
             ++m->launches;
         } else {  // large levels: the sweep's neighbours read one array instead of three
-            k_prolong<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
-            k_jacobi<T><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+            launch_dep(k_prolong<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
+            launch_dep(k_jacobi<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
                                                              B::diag(L), B::x(L), B::b(L), B::x2(L), st);
             m->launches += 2;
         }
     }
     const T *x0 = amg.nlev > 1 ? B::x2(L0) : B::x(L0);
     if (pa)
-        k_flip_out_dots<T><<<kRedBlocks, kThreads, 0, s>>>(nc, x0, 1.0 / amg.scale, z, res, rp, pa, pb, st);
+        launch_dep(k_flip_out_dots<T>, kRedBlocks, kThreads, s, nc, x0, 1.0 / amg.scale, z, res, rp, pa, pb, st);
     else
-        k_flip_out<T><<<blocks_for(L0.n), kThreads, 0, s>>>(nc, x0, 1.0 / amg.scale, z, st);
+        launch_dep(k_flip_out<T>, blocks_for(L0.n), kThreads, s, nc, x0, 1.0 / amg.scale, z, st);
     ++m->launches;
 }
 

@@ -45,6 +45,15 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *slot, doub
     atomicMax(slot, static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+// Programmatic dependent launch: wait until the kernel before this one in the
+// stream has completed and its writes are visible (a no-op when this kernel
+// was launched without the attribute), then allow the next kernel's blocks to
+// be scheduled while this one runs; they wait the same way before reading.
+__device__ __forceinline__ void dep_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Deterministic block sum: warp shuffles, then one warp over the warp sums.
 // Every thread of the block must call it; the result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {

@@ -185,6 +185,23 @@ template <class T> inline T *ptr(Buf &b) { return static_cast<T *>(b.p); }
 // one partial sum per block).
 constexpr int kRedBlocks = 152 * 8;
 
+// Launch of a kernel that begins with dep_enter(): it may be scheduled while
+// the previous kernel in the stream drains (programmatic dependent launch).
+template <typename... P, typename... A>
+inline void launch_dep(void (*kernel)(P...), int grid, int block, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 inline int blocks_for(int64_t n, int threads = kThreads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

@@ -307,6 +307,7 @@ __global__ void k_copy(int64_t n, const double *in, double *out, const CgState *
 
 // z = res / diag (Jacobi preconditioner)
 __global__ void k_jacobi_precond(int64_t n, const double *diag, const double *res, double *z, const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) z[i] = res[i] / diag[i];
 }
@@ -334,6 +335,7 @@ __global__ void k_cg_start(const double *partials, int nparts, double target, Cg
 __global__ void k_cg_matvec(int64_t nc, const int64_t *row_ptr, const int32_t *col, const int64_t *col_ptr,
                             const int32_t *csc_row, const double *a2, const double *a2c, const double *diag,
                             const double *p, double *q, double *partials, const CgState *st) {
+    dep_enter();
     if (st->converged) return;
     double acc = 0.0;
     GRID_STRIDE(l, 2 * nc) {
@@ -352,6 +354,7 @@ __global__ void k_cg_matvec(int64_t nc, const int64_t *row_ptr, const int32_t *c
 }
 
 __global__ void k_cg_alpha(const double *partials, int nparts, CgState *st) {
+    dep_enter();
     if (st->converged) return;
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partials[i];
@@ -366,6 +369,7 @@ __global__ void k_cg_alpha(const double *partials, int nparts, CgState *st) {
 // sums of |res|
 __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double *d, double *res, double *rp,
                             double *partials, const CgState *st) {
+    dep_enter();
     if (st->converged) return;
     const double alpha = st->alpha;
     double l1 = 0.0;
@@ -387,6 +391,7 @@ __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double
 template <class T>
 __global__ void k_cg_update_b(int64_t nc, const double *p, const double *q, double *d, double *res, double *rp,
                               double *partials, T *b, const CgState *st) {
+    dep_enter();
     if (st->converged) return;
     const double alpha = st->alpha;
     double l1 = 0.0;
@@ -407,6 +412,7 @@ __global__ void k_cg_update_b(int64_t nc, const double *p, const double *q, doub
 // preconditioner may differ slightly between applications)
 __global__ void k_dot2(int64_t n, const double *z, const double *res, const double *rp, double *pa, double *pb,
                        const CgState *st) {
+    dep_enter();
     if (st && st->converged) return;
     double a = 0.0, b = 0.0;
     GRID_STRIDE(i, n) {
@@ -423,6 +429,7 @@ __global__ void k_dot2(int64_t n, const double *z, const double *res, const doub
 
 __global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const double *l1_parts, int nparts,
                           CgState *st) {
+    dep_enter();
     if (st->converged) return;
     double rz = 0.0, zp = 0.0, l1 = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -443,6 +450,7 @@ __global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const 
 }
 
 __global__ void k_cg_pupdate(int64_t n2, const double *z, double *p, const CgState *st) {
+    dep_enter();
     if (st->converged) return;
     const double beta = st->beta;
     GRID_STRIDE(l, n2) p[l] = z[l] + beta * p[l];
@@ -613,29 +621,29 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         const int batch = amg ? 8 : 32;
         auto enqueue_batch = [&]() {
             for (int k = 0; k < batch; ++k) {
-                k_cg_matvec<<<kRedBlocks, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                launch_dep(k_cg_matvec, kRedBlocks, kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
                                                            ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2,
                                                            a2c, diag, p, q, part, st);
-                k_cg_alpha<<<1, 1024, 0, s>>>(part, kRedBlocks, st);
+                launch_dep(k_cg_alpha, 1, 1024, s, part, kRedBlocks, st);
                 if (amg) {
                     // the update also writes the V-cycle's right-hand side; the
                     // V-cycle's last kernel also forms the two dot products
                     if (fp32)
-                        k_cg_update_b<float><<<kRedBlocks, kThreads, 0, s>>>(
+                        launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, 
                             nc, p, q, d, res, rp, part_l1, static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
                     else
-                        k_cg_update_b<double><<<kRedBlocks, kThreads, 0, s>>>(
+                        launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, 
                             nc, p, q, d, res, rp, part_l1, static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
                     precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
                     m->launches += 3;
                 } else {
-                    k_cg_update<<<kRedBlocks, kThreads, 0, s>>>(n2, p, q, d, res, rp, part_l1, st);
+                    launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, part_l1, st);
                     precondition(m, amg, fp32, res, z, st);
-                    k_dot2<<<kRedBlocks, kThreads, 0, s>>>(n2, z, res, rp, part_rz, part_zp, st);
+                    launch_dep(k_dot2, kRedBlocks, kThreads, s, n2, z, res, rp, part_rz, part_zp, st);
                     m->launches += 4;
                 }
-                k_cg_beta<<<1, 1024, 0, s>>>(part_rz, part_zp, part_l1, kRedBlocks, st);
-                k_cg_pupdate<<<bl, kThreads, 0, s>>>(n2, z, p, st);
+                launch_dep(k_cg_beta, 1, 1024, s, part_rz, part_zp, part_l1, kRedBlocks, st);
+                launch_dep(k_cg_pupdate, bl, kThreads, s, n2, z, p, st);
                 m->launches += 2;
             }
         };

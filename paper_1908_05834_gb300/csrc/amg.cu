@@ -64,12 +64,14 @@ constexpr int kLargeCoarsestSweeps = 20;
 // column node nc + j: from column j (rows i).  Values -a_ij^2.
 __global__ void k_level0_ptr(int64_t nc, int64_t nnz, const int64_t *row_ptr, const int64_t *col_ptr,
                              int64_t *ptr0) {
+    dep_enter();
     GRID_STRIDE(l, 2 * nc + 1) ptr0[l] = l <= nc ? row_ptr[l] : nnz + col_ptr[l - nc];
 }
 
 __global__ void k_level0_fill(int64_t nc, const int64_t *row_ptr, const int32_t *col, const int64_t *col_ptr,
                               const int32_t *csc_row, const double *a2, const double *a2c, const int64_t *ptr0,
                               int32_t *col0, double *val0) {
+    dep_enter();
     GRID_STRIDE(l, 2 * nc) {
         int64_t dst = ptr0[l];
         if (l < nc) {
@@ -123,6 +125,7 @@ __device__ __forceinline__ bool ranks_above(int64_t i, int32_t j, double w, int3
 // still unpaired.
 __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
                            const int32_t *partner, int only_free, int32_t *best) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         int32_t b = -1;
         int bc = 0;
@@ -150,6 +153,7 @@ __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, co
 }
 
 __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         if (partner[i] >= 0) continue;
         const int32_t b = best[i];
@@ -164,6 +168,7 @@ __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
 // hub should follow the hub.
 __global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
                                 const double *diag, int32_t *att) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         int32_t b = -1;
         int bc = 0;
@@ -193,6 +198,7 @@ __global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *co
 // pair; every other node is left open (-2) for the second pass.
 __global__ void k_leaders1(int64_t n, const int64_t *ptr, const int32_t *partner, const int32_t *att, int32_t *leader,
                            int *isolated) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         int32_t lead = -2;
         if (ptr[i + 1] == ptr[i]) {
@@ -215,6 +221,7 @@ __global__ void k_leaders1(int64_t n, const int64_t *ptr, const int32_t *partner
 // want[i]: the attachment target of an open node when that target is open
 // too, else -1.
 __global__ void k_want(int64_t n, const int32_t *att, const int32_t *leader, int32_t *want) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         const int32_t t = att[i];
         want[i] = (leader[i] == -2 && t >= 0 && leader[t] == -2) ? t : -1;
@@ -226,6 +233,7 @@ __global__ void k_want(int64_t n, const int32_t *att, const int32_t *leader, int
 // it; every other open node leads itself.  Each leader leads itself, so
 // aggregates have no chains.  is_leader flags the leaders for the scan.
 __global__ void k_leaders2(int64_t n, const int32_t *want, int32_t *leader, int32_t *is_leader) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         int32_t lead = leader[i];
         if (lead == -2) {
@@ -246,6 +254,7 @@ __global__ void k_leaders2(int64_t n, const int32_t *want, int32_t *leader, int3
 
 __global__ void k_aggregates(int64_t n, const int32_t *leader, const int64_t *leader_pos, int32_t *agg,
                              int32_t *count) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         if (leader[i] < 0) {
             agg[i] = -1;
@@ -258,6 +267,7 @@ __global__ void k_aggregates(int64_t n, const int32_t *leader, const int64_t *le
 }
 
 __global__ void k_members_fill(int64_t n, const int32_t *agg, const int64_t *mptr, int32_t *fill, int32_t *mlist) {
+    dep_enter();
     GRID_STRIDE(i, n) {
         const int32_t I = agg[i];
         if (I < 0) continue;
@@ -267,6 +277,7 @@ __global__ void k_members_fill(int64_t n, const int32_t *agg, const int64_t *mpt
 
 // Members of each aggregate in increasing node order (small insertion sort).
 __global__ void k_members_sort(int64_t nco, const int64_t *mptr, int32_t *mlist) {
+    dep_enter();
     GRID_STRIDE(I, nco) {
         const int64_t b = mptr[I], e = mptr[I + 1];
         for (int64_t p = b + 1; p < e; ++p) {
@@ -322,6 +333,7 @@ __device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
 __global__ void k_coarse_count_thread(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
                                       const int32_t *col, const double *val, const double *exc, const int32_t *agg,
                                       int32_t *rowcnt, int *overflow) {
+    dep_enter();
     int32_t cbuf[kCoarseCap];
     double vbuf[kCoarseCap];
     GRID_STRIDE(I, nco) {
@@ -339,6 +351,7 @@ __global__ void k_coarse_count_thread(int64_t nco, const int64_t *mptr, const in
 __global__ void k_coarse_fill_thread(int64_t nco, const int64_t *mptr, const int32_t *mlist, const int64_t *ptr,
                                      const int32_t *col, const double *val, const double *exc, const int32_t *agg,
                                      const int64_t *cptr, int32_t *ccol, double *cval, double *cdiag, double *cexc) {
+    dep_enter();
     int32_t cbuf[kCoarseCap];
     double vbuf[kCoarseCap];
     GRID_STRIDE(I, nco) {
@@ -462,6 +475,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_count(int64_t nco, 
                                                                    const int32_t *col, const double *val,
                                                                    const double *exc, const int32_t *agg,
                                                                    int32_t *rowcnt, int *overflow) {
+    dep_enter();
     __shared__ MergeSmem sm_all[kMergeWarps];
     MergeSmem &sm = sm_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -502,6 +516,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_coarse_fill(int64_t nco, c
                                                                   const double *exc, const int32_t *agg,
                                                                   const int64_t *cptr, int32_t *ccol, double *cval,
                                                                   double *cdiag, double *cexc) {
+    dep_enter();
     __shared__ MergeSmem sm_all[kMergeWarps];
     MergeSmem &sm = sm_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -551,11 +566,11 @@ static void coarse_count(bchar_mesh_t m, const AmgLevel &F, const AmgLevel &C, i
     AmgLevel &Fm = const_cast<AmgLevel &>(F);
     AmgLevel &Cm = const_cast<AmgLevel &>(C);
     if (wide_rows(F))
-        k_coarse_count<<<blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, m->stream>>>(
+        launch_dep(k_coarse_count, blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, m->stream, 
             ncoarse, ptr<int64_t>(Cm.mptr), ptr<int32_t>(Cm.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
             ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), rowcnt, overflow);
     else
-        k_coarse_count_thread<<<blocks_for(ncoarse, 128), 128, 0, m->stream>>>(
+        launch_dep(k_coarse_count_thread, blocks_for(ncoarse, 128), 128, m->stream, 
             ncoarse, ptr<int64_t>(Cm.mptr), ptr<int32_t>(Cm.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
             ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), rowcnt, overflow);
     ++m->launches;
@@ -564,12 +579,12 @@ static void coarse_count(bchar_mesh_t m, const AmgLevel &F, const AmgLevel &C, i
 static void coarse_fill(bchar_mesh_t m, const AmgLevel &F, AmgLevel &C, int64_t ncoarse, const double *fexc) {
     AmgLevel &Fm = const_cast<AmgLevel &>(F);
     if (wide_rows(F))
-        k_coarse_fill<<<blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, 0, m->stream>>>(
+        launch_dep(k_coarse_fill, blocks_for(ncoarse * 32, 32 * kMergeWarps), 32 * kMergeWarps, m->stream, 
             ncoarse, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
             ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
             ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
     else
-        k_coarse_fill_thread<<<blocks_for(ncoarse, 128), 128, 0, m->stream>>>(
+        launch_dep(k_coarse_fill_thread, blocks_for(ncoarse, 128), 128, m->stream, 
             ncoarse, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), ptr<int64_t>(Fm.ptr), ptr<int32_t>(Fm.col),
             ptr<double>(Fm.val), fexc, ptr<int32_t>(Fm.agg), ptr<int64_t>(C.ptr), ptr<int32_t>(C.col),
             ptr<double>(C.val), ptr<double>(C.diag), ptr<double>(C.exc));
@@ -585,6 +600,7 @@ static void coarse_fill(bchar_mesh_t m, const AmgLevel &F, AmgLevel &C, int64_t 
 // is far faster than FP64) and in FP64 for the last digits.
 
 template <class T> __global__ void k_scaled_copy(int64_t n, const double *in, T *out, double inv_scale) {
+    dep_enter();
     GRID_STRIDE(i, n) out[i] = static_cast<T>(in[i] * inv_scale);
 }
 
@@ -809,9 +825,9 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         AmgLevel &L0 = amg.levels[0];
         L0.nnz = 2 * nnz;
         if (!ensure(m, L0.col, sizeof(int32_t) * L0.nnz) || !ensure(m, L0.val, sizeof(double) * L0.nnz)) return false;
-        k_level0_ptr<<<blocks_for(L0.n + 1), kThreads, 0, s>>>(nc, nnz, ptr<int64_t>(m->row_ptr),
+        launch_dep(k_level0_ptr, blocks_for(L0.n + 1), kThreads, s, nc, nnz, ptr<int64_t>(m->row_ptr),
                                                                ptr<int64_t>(m->col_ptr), ptr<int64_t>(L0.ptr));
-        k_level0_fill<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+        launch_dep(k_level0_fill, blocks_for(L0.n), kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
                                                             ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
                                                             ptr<double>(m->a2), ptr<double>(m->a2c),
                                                             ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
@@ -831,9 +847,9 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         return false;
     L0.diag_ext = ptr<double>(m->diag);
     L0.exc_ext = ptr<double>(m->qexc);
-    k_level0_ptr<<<blocks_for(L0.n + 1), kThreads, 0, s>>>(nc, nnz, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
+    launch_dep(k_level0_ptr, blocks_for(L0.n + 1), kThreads, s, nc, nnz, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
                                                            ptr<int64_t>(L0.ptr));
-    k_level0_fill<<<blocks_for(L0.n), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+    launch_dep(k_level0_fill, blocks_for(L0.n), kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
                                                         ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
                                                         ptr<double>(m->a2), ptr<double>(m->a2c),
                                                         ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
@@ -858,16 +874,16 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * F.n, s);
         cudaMemsetAsync(overflow, 0, 2 * sizeof(int), s);
         for (int round = 0; round < kHandshakes; ++round) {
-            k_heaviest<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
+            launch_dep(k_heaviest, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
                                                fdg, partner, round > 0, best);
-            k_handshake<<<bl, kThreads, 0, s>>>(F.n, best, partner);
+            launch_dep(k_handshake, bl, kThreads, s, F.n, best, partner);
             m->launches += 2;
         }
-        k_attach_target<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val), fdg,
+        launch_dep(k_attach_target, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val), fdg,
                                                 att);
-        k_leaders1<<<bl, kThreads, 0, s>>>(F.n, ptr<int64_t>(F.ptr), partner, att, leader, isolated);
-        k_want<<<bl, kThreads, 0, s>>>(F.n, att, leader, want);
-        k_leaders2<<<bl, kThreads, 0, s>>>(F.n, want, leader, flag);
+        launch_dep(k_leaders1, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), partner, att, leader, isolated);
+        launch_dep(k_want, bl, kThreads, s, F.n, att, leader, want);
+        launch_dep(k_leaders2, bl, kThreads, s, F.n, want, leader, flag);
         m->launches += 4;
         // leader positions: scan of the leader flags (int32 -> int64), reuse the
         // per-level x buffer as int64 scratch (it holds n + 1 entries)
@@ -890,12 +906,12 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
             return false;
         // aggregates: map, member counts -> pointers, members sorted by node
         cudaMemsetAsync(flag, 0, sizeof(int32_t) * U, s);
-        k_aggregates<<<bl, kThreads, 0, s>>>(Fr.n, leader, pos, ptr<int32_t>(Fr.agg), flag);
+        launch_dep(k_aggregates, bl, kThreads, s, Fr.n, leader, pos, ptr<int32_t>(Fr.agg), flag);
         scan_i32_to_i64(m, flag, ptr<int64_t>(C.mptr), U);
         cudaMemsetAsync(flag, 0, sizeof(int32_t) * U, s);
-        k_members_fill<<<bl, kThreads, 0, s>>>(Fr.n, ptr<int32_t>(Fr.agg), ptr<int64_t>(C.mptr), flag,
+        launch_dep(k_members_fill, bl, kThreads, s, Fr.n, ptr<int32_t>(Fr.agg), ptr<int64_t>(C.mptr), flag,
                                                ptr<int32_t>(C.mlist));
-        k_members_sort<<<blocks_for(U), kThreads, 0, s>>>(U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
+        launch_dep(k_members_sort, blocks_for(U), kThreads, s, U, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist));
         m->launches += 3;
         int32_t *rowcnt = flag;
         coarse_count(m, Fr, C, U, fexc, rowcnt, overflow);
@@ -938,12 +954,12 @@ static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg) {
         if (!ensure(m, L.dval, sizeof(double) * nnzl) || !ensure(m, L.ddiag, sizeof(double) * L.n)) return false;
         const double *dg = L.diag_ext ? L.diag_ext : ptr<double>(L.diag);
         if (L.nnz > 0) {
-            k_scaled_copy<float><<<blocks_for(L.nnz), kThreads, 0, s>>>(L.nnz, ptr<double>(L.val), ptr<float>(L.fval), inv);
-            k_scaled_copy<double><<<blocks_for(L.nnz), kThreads, 0, s>>>(L.nnz, ptr<double>(L.val), ptr<double>(L.dval),
+            launch_dep(k_scaled_copy<float>, blocks_for(L.nnz), kThreads, s, L.nnz, ptr<double>(L.val), ptr<float>(L.fval), inv);
+            launch_dep(k_scaled_copy<double>, blocks_for(L.nnz), kThreads, s, L.nnz, ptr<double>(L.val), ptr<double>(L.dval),
                                                                          inv);
         }
-        k_scaled_copy<float><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, dg, ptr<float>(L.fdiag), inv);
-        k_scaled_copy<double><<<blocks_for(L.n), kThreads, 0, s>>>(L.n, dg, ptr<double>(L.ddiag), inv);
+        launch_dep(k_scaled_copy<float>, blocks_for(L.n), kThreads, s, L.n, dg, ptr<float>(L.fdiag), inv);
+        launch_dep(k_scaled_copy<double>, blocks_for(L.n), kThreads, s, L.n, dg, ptr<double>(L.ddiag), inv);
         m->launches += 4;
     }
     return true;

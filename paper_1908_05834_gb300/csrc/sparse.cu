@@ -33,6 +33,7 @@ namespace bchar {
 // ---------------------------------------------------------------- scan
 
 __global__ void k_scan_partial(const int32_t *in, int64_t n, int64_t *block_sums) {
+    dep_enter();
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanChunk;
     int64_t s = 0;
     for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
@@ -49,6 +50,7 @@ __global__ void k_scan_partial(const int32_t *in, int64_t n, int64_t *block_sums
 
 // One block: exclusive scan of nb block sums in place, total in sums[nb].
 __global__ void k_scan_top(int64_t *sums, int nb) {
+    dep_enter();
     __shared__ int64_t sh[1024];
     __shared__ int64_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -73,6 +75,7 @@ __global__ void k_scan_top(int64_t *sums, int nb) {
 }
 
 __global__ void k_scan_final(const int32_t *in, int64_t n, const int64_t *block_off, int64_t *out, int nb) {
+    dep_enter();
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanChunk;
     constexpr int per = kScanChunk / kThreads;
     const int64_t mine = base + static_cast<int64_t>(threadIdx.x) * per;
@@ -104,9 +107,9 @@ void scan_i32_to_i64(bchar_mesh_t m, const int32_t *in, int64_t *out, int64_t n)
     const int nbb = nb < 1 ? 1 : nb;
     ensure(m, m->scan_tmp, sizeof(int64_t) * (nbb + 1));
     int64_t *sums = ptr<int64_t>(m->scan_tmp);
-    k_scan_partial<<<nbb, kThreads, 0, m->stream>>>(in, n, sums);
-    k_scan_top<<<1, 1024, 0, m->stream>>>(sums, nbb);
-    k_scan_final<<<nbb, kThreads, 0, m->stream>>>(in, n, sums, out, nbb);
+    launch_dep(k_scan_partial, nbb, kThreads, m->stream, in, n, sums);
+    launch_dep(k_scan_top, 1, 1024, m->stream, sums, nbb);
+    launch_dep(k_scan_final, nbb, kThreads, m->stream, in, n, sums, out, nbb);
     m->launches += 3;
 }
 

@@ -73,7 +73,7 @@ template <class real> struct BallSmem {
 // Sum over the balls of residing cell M (cell coordinates mc) of
 // rho_M phi_M |B_hat cap B_{M,m}| for a tracked ball of radius rh at position p
 // relative to the corner of cell tc.
-template <class real>
+template <class real, int DIM>
 __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc[3], const real p[3], real rh,
                                                  const int mc[3], int64_t M) {
     int cnt[3];
@@ -81,7 +81,8 @@ __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc
     const real rM = Real<real>::rad(m, M);
     const real rp = Real<real>::rhophi(m, M);
     real o[3] = {real(0), real(0), real(0)}, wM[3] = {real(0), real(0), real(0)};
-    for (int a = 0; a < m.dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
         o[a] = static_cast<real>(m.x[a][mc[a]] - m.x[a][tc[a]]) - p[a];
         wM[a] = Real<real>::w(m, a)[mc[a]];
     }
@@ -90,7 +91,8 @@ __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc
     // reach from the tracked centre holds no overlapping ball (the loop below
     // would return exactly 0); the margin keeps the test conservative
     real dist2 = real(0);
-    for (int a = 0; a < m.dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
         const real g = o[a] > real(0) ? o[a] : (o[a] + wM[a] < real(0) ? -(o[a] + wM[a]) : real(0));
         dist2 += g * g;
     }
@@ -98,13 +100,13 @@ __device__ __forceinline__ real ball_cell_weight(const MeshView &m, const int tc
     if (dist2 > lim * lim) return real(0);
     real sum = real(0);
     for (int sz = 0; sz < cnt[2]; ++sz) {
-        real dz = m.dim == 3 ? o[2] + (real(sz) + real(0.5)) * wM[2] / real(cnt[2]) : real(0);
+        real dz = DIM == 3 ? o[2] + (real(sz) + real(0.5)) * wM[2] / real(cnt[2]) : real(0);
         for (int sy = 0; sy < cnt[1]; ++sy) {
             real dy = o[1] + (real(sy) + real(0.5)) * wM[1] / real(cnt[1]);
             for (int sx = 0; sx < cnt[0]; ++sx) {
                 real dx = o[0] + (real(sx) + real(0.5)) * wM[0] / real(cnt[0]);
                 real d = sqrt(dx * dx + dy * dy + dz * dz);
-                if (d < reach) sum += rp * lens<real>(m.dim, d, rh, rM);
+                if (d < reach) sum += rp * lens<real>(DIM, d, rh, rM);
             }
         }
     }
@@ -118,8 +120,8 @@ __device__ __forceinline__ int box_index(const BallSmem<real> &sm, int s, const 
     return ((mc[2] - sm.lo[s][2]) * wy + (mc[1] - sm.lo[s][1])) * wx + (mc[0] - sm.lo[s][0]);
 }
 
-template <class real>
-__global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_cell, const real *t_xi,
+template <class real, int DIM>
+__global__ void __launch_bounds__(256, 3) k_assemble(MeshView m, const int32_t *t_cell, const real *t_xi,
                                                   const real *t_rhat, double drop_tol, int row_cap, int win_cap,
                                                   int32_t *slab_col, double *slab_val, int32_t *row_len,
                                                   DevInfo *info) {
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
                 sm.lo[lane][a] = c[a];
                 sm.hi[lane][a] = c[a];
             }
-            for (int a = 0; a < m.dim; ++a) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
                 const real *w = Real<real>::w(m, a);
                 p[a] = t_xi[3 * b + a] * w[c[a]];
                 int lo = c[a];
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
                 const int t = q - sm.poff[s];
                 const int wx = sm.hi[s][0] - sm.lo[s][0] + 1, wy = sm.hi[s][1] - sm.lo[s][1] + 1;
                 int mc[3] = {sm.lo[s][0] + t % wx, sm.lo[s][1] + (t / wx) % wy, sm.lo[s][2] + t / (wx * wy)};
-                sm.S[q] = ball_cell_weight<real>(m, sm.c[s], sm.p[s], sm.rh[s], mc, flat_cell(m, mc));
+                sm.S[q] = ball_cell_weight<real, DIM>(m, sm.c[s], sm.p[s], sm.rh[s], mc, flat_cell(m, mc));
             }
             __syncwarp();
             if (lane < nK) {
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
             for (mc[2] = sm.lo[lane][2]; mc[2] <= sm.hi[lane][2]; ++mc[2])
                 for (mc[1] = sm.lo[lane][1]; mc[1] <= sm.hi[lane][1]; ++mc[1])
                     for (mc[0] = sm.lo[lane][0]; mc[0] <= sm.hi[lane][0]; ++mc[0])
-                        den += ball_cell_weight<real>(m, sm.c[lane], sm.p[lane], sm.rh[lane], mc, flat_cell(m, mc));
+                        den += ball_cell_weight<real, DIM>(m, sm.c[lane], sm.p[lane], sm.rh[lane], mc, flat_cell(m, mc));
             sm.den[lane] = den;
             if (den == real(0)) atomicAdd(&info->void_balls, 1);
         }
@@ -249,11 +252,12 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
                 M = flat_cell(m, mc);
                 for (int s = 0; s < nK; ++s) {
                     bool in = true;
-                    for (int a = 0; a < m.dim; ++a) in = in && mc[a] >= sm.lo[s][a] && mc[a] <= sm.hi[s][a];
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) in = in && mc[a] >= sm.lo[s][a] && mc[a] <= sm.hi[s][a];
                     if (!in) continue;
                     if (sm.den[s] > real(0)) {
                         const real S = table ? sm.S[sm.poff[s] + box_index(sm, s, mc)]
-                                             : ball_cell_weight<real>(m, sm.c[s], sm.p[s], sm.rh[s], mc, M);
+                                             : ball_cell_weight<real, DIM>(m, sm.c[s], sm.p[s], sm.rh[s], mc, M);
                         V += mK * static_cast<double>(S / sm.den[s]);
                     } else if (mc[0] == sm.c[s][0] && mc[1] == sm.c[s][1] && mc[2] == sm.c[s][2]) {
                         V += mK;
@@ -282,21 +286,30 @@ __global__ void __launch_bounds__(256) k_assemble(MeshView m, const int32_t *t_c
 
 MeshView full_view(bchar_mesh_t m);
 
+template <class real, int DIM>
+static void assemble_in(bchar_mesh_t m, const MeshView &mv, int win_cap, int blocks) {
+    k_assemble<real, DIM><<<blocks, 256, 0, m->stream>>>(mv, ptr<int32_t>(m->t_cell), ptr<real>(m->t_xi),
+                                                         ptr<real>(m->t_rhat), m->opt.drop_tol, m->row_cap, win_cap,
+                                                         ptr<int32_t>(m->slab_col), ptr<double>(m->slab_val),
+                                                         ptr<int32_t>(m->row_len), ptr<DevInfo>(m->dinfo));
+}
+
 void launch_assemble(bchar_mesh_t m) {
     MeshView mv = full_view(m);
     const int win_cap = m->dim == 2 ? 4096 : 32768;
     const int blocks = blocks_for(m->nc * 32, 256);
-    if (m->opt.precision == BCHAR_FP32_SPLIT)
-        k_assemble<float><<<blocks, 256, 0, m->stream>>>(mv, ptr<int32_t>(m->t_cell), ptr<float>(m->t_xi),
-                                                         ptr<float>(m->t_rhat), m->opt.drop_tol, m->row_cap, win_cap,
-                                                         ptr<int32_t>(m->slab_col), ptr<double>(m->slab_val),
-                                                         ptr<int32_t>(m->row_len), ptr<DevInfo>(m->dinfo));
-    else
-        k_assemble<double><<<blocks, 256, 0, m->stream>>>(mv, ptr<int32_t>(m->t_cell), ptr<double>(m->t_xi),
-                                                          ptr<double>(m->t_rhat), m->opt.drop_tol, m->row_cap,
-                                                          win_cap, ptr<int32_t>(m->slab_col),
-                                                          ptr<double>(m->slab_val), ptr<int32_t>(m->row_len),
-                                                          ptr<DevInfo>(m->dinfo));
+    const bool f32 = m->opt.precision == BCHAR_FP32_SPLIT;
+    if (m->dim == 2) {
+        if (f32)
+            assemble_in<float, 2>(m, mv, win_cap, blocks);
+        else
+            assemble_in<double, 2>(m, mv, win_cap, blocks);
+    } else {
+        if (f32)
+            assemble_in<float, 3>(m, mv, win_cap, blocks);
+        else
+            assemble_in<double, 3>(m, mv, win_cap, blocks);
+    }
     ++m->launches;
 }
 

@@ -369,7 +369,8 @@ bchar_status bchar_set_velocity_scaled(bchar_mesh_t m, const double *const *face
         return fail(m, BCHAR_ERR_DIVERGENCE, msg);
     }
     m->vmax = bits_to_double(h->vmax_bits);
-    const size_t rec_bytes = (m->opt.precision == BCHAR_FP32_SPLIT ? sizeof(float) : sizeof(double)) * 8 * m->nc;
+    const size_t rec_bytes =
+        (m->opt.precision == BCHAR_FP32_SPLIT ? sizeof(float) : sizeof(double)) * kRecordLen * m->nc;
     if (!ensure(m, m->rec, rec_bytes)) return BCHAR_ERR_OUT_OF_MEMORY;
     launch_cell_records(m);
     m->has_velocity = true;

@@ -54,9 +54,11 @@ struct MeshView {
 struct VelView {
     const double *u[3];
     const float *uf[3];
-    // one record of 8 values per cell: the lower and upper face velocity of
-    // each axis (0 for a missing axis), then phi (FP64 records) or 1 / phi
-    // (FP32 records), then 0; a tracking stage reads one record
+    // one record of kRecordLen values per cell: the lower and upper face
+    // velocity of each axis (0 for a missing axis), phi (FP64 records) or
+    // 1 / phi (FP32 records), 0, then the cell's width per axis (FP64) or
+    // inverse width (FP32), 0; a tracking stage reads the first 8 values, the
+    // first stage of a substep all 12
     const double *recd;
     const float *recf;
 };
@@ -180,6 +182,8 @@ void release(Buf &b);
 double total_volphi(bchar_mesh_t m);  // sum of |K|_phi over the mesh
 
 template <class T> inline T *ptr(Buf &b) { return static_cast<T *>(b.p); }
+
+constexpr int kRecordLen = 12;  // values per cell in the tracking records
 
 // Blocks of the reduction kernels of the conjugate gradients (grid-stride;
 // one partial sum per block).

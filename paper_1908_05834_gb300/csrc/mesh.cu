@@ -185,7 +185,8 @@ __global__ void k_cell_records(MeshView m, VelView v, real *rec) {
          k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         int c[3];
         split_cell(m, k, c);
-        real r[8] = {real(0), real(0), real(0), real(0), real(0), real(0), real(0), real(0)};
+        real r[kRecordLen];
+        for (int q = 0; q < kRecordLen; ++q) r[q] = real(0);
         for (int a = 0; a < m.dim; ++a) {
             int e[3] = {c[0], c[1], c[2]};
             int64_t len[3] = {m.n[0], m.n[1], m.n[2]};
@@ -197,7 +198,11 @@ __global__ void k_cell_records(MeshView m, VelView v, real *rec) {
             r[2 * a + 1] = Real<real>::u(v, a)[hi];
         }
         r[6] = sizeof(real) == 8 ? static_cast<real>(m.phi[k]) : static_cast<real>(1.0 / m.phi[k]);
-        for (int q = 0; q < 8; ++q) rec[8 * k + q] = r[q];
+        for (int a = 0; a < 3; ++a) {  // the cell's widths (FP64) or inverse widths (FP32); 1 for a missing axis
+            const double w = a < m.dim ? m.wd[a][c[a]] : 1.0;
+            r[8 + a] = sizeof(real) == 8 ? static_cast<real>(w) : static_cast<real>(1.0 / w);
+        }
+        for (int q = 0; q < kRecordLen; ++q) rec[kRecordLen * k + q] = r[q];
     }
 }
 

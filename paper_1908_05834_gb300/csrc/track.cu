@@ -52,32 +52,40 @@ __device__ __forceinline__ void relocate(const MeshView &m, int a, int &c, real 
 
 // Arithmetic of one stage in the tracking precision.  FP64 divides by phi and
 // by the width (the operations of a plain evaluation of the RT0 field); FP32
-// multiplies by 1 / phi from the cell's record and by the FP32 table of
-// 1 / width (both formed from FP64 values).
+// multiplies by 1 / phi and 1 / width, all read from the cell's record (and
+// formed from FP64 values).  A substep's moves and its final update use the
+// width terms of the point's cell at the start of the substep, loaded once.
 template <class real> struct Stage;
 template <> struct Stage<double> {
-    // r[0..5]: lower/upper face velocity per axis, r[6]: phi
+    // r[0..5]: lower/upper face velocity per axis, r[6]: phi; wr[0..2]: widths
     static __device__ __forceinline__ void load(const VelView &v, int64_t k, double r[7]) {
-        const double2 *p = reinterpret_cast<const double2 *>(v.recd + 8 * k);
+        const double2 *p = reinterpret_cast<const double2 *>(v.recd + kRecordLen * k);
         const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
         r[0] = a.x, r[1] = a.y, r[2] = b.x, r[3] = b.y, r[4] = c.x, r[5] = c.y, r[6] = d.x;
     }
-    static __device__ __forceinline__ double per_phi(double u, double phi) { return u / phi; }
-    static __device__ __forceinline__ double per_width(const MeshView &m, int a, int c, double d) {
-        return d / m.wd[a][c];
+    static __device__ __forceinline__ void load_widths(const VelView &v, int64_t k, double wr[3]) {
+        const double2 *p = reinterpret_cast<const double2 *>(v.recd + kRecordLen * k);
+        const double2 e = __ldg(p + 4), f = __ldg(p + 5);
+        wr[0] = e.x, wr[1] = e.y, wr[2] = f.x;
     }
+    static __device__ __forceinline__ double per_phi(double u, double phi) { return u / phi; }
+    // d over the width held in a record
+    static __device__ __forceinline__ double by_width(double wr, double d) { return d / wr; }
 };
 template <> struct Stage<float> {
-    // r[0..5]: lower/upper face velocity per axis, r[6]: 1 / phi
+    // r[0..5]: lower/upper face velocity per axis, r[6]: 1 / phi; wr[0..2]: inverse widths
     static __device__ __forceinline__ void load(const VelView &v, int64_t k, float r[7]) {
-        const float4 *p = reinterpret_cast<const float4 *>(v.recf + 8 * k);
+        const float4 *p = reinterpret_cast<const float4 *>(v.recf + kRecordLen * k);
         const float4 a = __ldg(p), b = __ldg(p + 1);
         r[0] = a.x, r[1] = a.y, r[2] = a.z, r[3] = a.w, r[4] = b.x, r[5] = b.y, r[6] = b.z;
     }
-    static __device__ __forceinline__ float per_phi(float u, float inv_phi) { return u * inv_phi; }
-    static __device__ __forceinline__ float per_width(const MeshView &m, int a, int c, float d) {
-        return d * __ldg(m.wif[a] + c);
+    static __device__ __forceinline__ void load_widths(const VelView &v, int64_t k, float wr[3]) {
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(v.recf + kRecordLen * k) + 2);
+        wr[0] = c.x, wr[1] = c.y, wr[2] = c.z;
     }
+    static __device__ __forceinline__ float per_phi(float u, float inv_phi) { return u * inv_phi; }
+    // d times the inverse width held in a record (the same value as m.wif)
+    static __device__ __forceinline__ float by_width(float wr, float d) { return d * wr; }
 };
 
 // Flat index of a cell (32-bit: meshes hold fewer than 2^31 cells).
@@ -101,10 +109,11 @@ __device__ __forceinline__ void flow(const MeshView &m, const VelView &v, const 
     }
 }
 
-// (c2, x2) = (c, xi) moved by the physical displacement s * k.
+// (c2, x2) = (c, xi) moved by the physical displacement s * k; wb holds the
+// width terms of cell c (from its record).
 template <class real, int DIM>
 __device__ __forceinline__ void moved(const MeshView &m, const int (&c)[3], const real (&xi)[3], real s,
-                                      const real (&k)[3], int (&c2)[3], real (&x2)[3]) {
+                                      const real (&k)[3], const real (&wb)[3], int (&c2)[3], real (&x2)[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         c2[a] = c[a];
@@ -112,7 +121,7 @@ __device__ __forceinline__ void moved(const MeshView &m, const int (&c)[3], cons
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        x2[a] = xi[a] + Stage<real>::per_width(m, a, c[a], s * k[a]);
+        x2[a] = xi[a] + Stage<real>::by_width(wb[a], s * k[a]);
         relocate<real>(m, a, c2[a], x2[a]);
     }
 }
@@ -122,15 +131,18 @@ __device__ void rk4(const MeshView &m, const VelView &v, int (&c)[P][3], real (&
                     real sign) {
     const real half = real(0.5) * h;
     for (int st = 0; st < substeps; ++st) {
-        real acc[P][3], k[P][3], x2[P][3];
+        real acc[P][3], k[P][3], x2[P][3], wb[P][3];
         int c2[P][3];
 #pragma unroll
-        for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c[p], xi[p], sign, k[p]);
+        for (int p = 0; p < P; ++p) {
+            flow<real, DIM>(m, v, c[p], xi[p], sign, k[p]);
+            Stage<real>::load_widths(v, cell_of<DIM>(m, c[p]), wb[p]);
+        }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[p][a] = k[p][a];
-            moved<real, DIM>(m, c[p], xi[p], half, k[p], c2[p], x2[p]);
+            moved<real, DIM>(m, c[p], xi[p], half, k[p], wb[p], c2[p], x2[p]);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
@@ -138,7 +150,7 @@ __device__ void rk4(const MeshView &m, const VelView &v, int (&c)[P][3], real (&
         for (int p = 0; p < P; ++p) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[p][a] = acc[p][a] + real(2) * k[p][a];
-            moved<real, DIM>(m, c[p], xi[p], half, k[p], c2[p], x2[p]);
+            moved<real, DIM>(m, c[p], xi[p], half, k[p], wb[p], c2[p], x2[p]);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
@@ -146,7 +158,7 @@ __device__ void rk4(const MeshView &m, const VelView &v, int (&c)[P][3], real (&
         for (int p = 0; p < P; ++p) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[p][a] = acc[p][a] + real(2) * k[p][a];
-            moved<real, DIM>(m, c[p], xi[p], h, k[p], c2[p], x2[p]);
+            moved<real, DIM>(m, c[p], xi[p], h, k[p], wb[p], c2[p], x2[p]);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) flow<real, DIM>(m, v, c2[p], x2[p], sign, k[p]);
@@ -155,7 +167,7 @@ __device__ void rk4(const MeshView &m, const VelView &v, int (&c)[P][3], real (&
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
                 const real d = h / real(6) * (acc[p][a] + k[p][a]);
-                xi[p][a] = xi[p][a] + Stage<real>::per_width(m, a, c[p][a], d);
+                xi[p][a] = xi[p][a] + Stage<real>::by_width(wb[p][a], d);
                 relocate<real>(m, a, c[p][a], xi[p][a]);
             }
         }

@@ -349,3 +349,25 @@ def test_balanced_targets_by_hand():
     A1 = sp.csr_matrix(np.array([[0.6, 0.4], [0.4, 0.6]]))
     b1, n1 = oracle.balanced_targets(A1, np.array([0.3, 0.7]))
     assert n1 == 0 and np.array_equal(b1, [0.3, 0.7])
+
+
+def test_column_fix_by_hand():
+    """The column fix (reading of eq. volAdj's first half after the bounds):
+    every column is scaled to its global target; a column whose entries were
+    all clipped to zero takes its A^(N) entries before that scaling."""
+    AN = sp.csr_matrix(np.array([[0.5, 0.2, 0.0],
+                                 [0.1, 0.3, 0.4],
+                                 [0.0, 0.1, 0.6]]))
+    Aq = AN.copy()
+    Aq.data = AN.data * np.array([1.2, 0.0, 0.9, 0.0, 0.8, 0.0, 1.1])  # column 1 fully clipped
+    Aq.data[Aq.data == 0.0] = 0.0
+    target = np.array([0.7, 0.9, 1.3])
+    A = oracle.column_fix(Aq, AN, target).toarray()
+    # column 0: (0.6, 0.09) scaled to 0.7; column 1: A^(N) (0.2, 0.3, 0.1) scaled to 0.9;
+    # column 2: (0.32, 0.66) scaled to 1.3
+    exp = np.zeros((3, 3))
+    exp[:, 0] = np.array([0.6, 0.09, 0.0]) * (0.7 / 0.69)
+    exp[:, 1] = np.array([0.2, 0.3, 0.1]) * (0.9 / 0.6)
+    exp[:, 2] = np.array([0.0, 0.32, 0.66]) * (1.3 / 0.98)
+    assert np.allclose(A, exp, rtol=1e-14, atol=0)
+    assert np.allclose(A.sum(axis=0), target, rtol=1e-14)

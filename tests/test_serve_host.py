@@ -115,3 +115,31 @@ def test_serving_stream_recipe():
         umax, phimin = (1.0, 1.0) if r.dim == 2 else (2.0, 0.1)
         assert r.amplitude * umax * r.dt * r.n / phimin == pytest.approx(r.cfl, rel=1e-12)
     assert serving_requests(8) == serving_requests(8)  # seeded
+
+
+def test_serving_request_payloads():
+    """The arrays of a 2D and a 3D request: RT0 face counts, porosity ranges,
+    c0 in [0, 1], the scaled time factor and a divergence-free base field."""
+    import math
+    import numpy as np
+    rs = serving_requests(64)
+    r2 = next(r for r in rs if r.dim == 2 and r.n <= 200)
+    r3 = next(r for r in rs if r.dim == 3 and r.n <= 48)
+    for r in (r2, r3):
+        coords, phi, faces, c0 = r.materialize()
+        n = r.n
+        assert len(coords) == r.dim and all(len(c) == n + 1 for c in coords)
+        assert phi.shape == (n ** r.dim,) and c0.shape == (n ** r.dim,)
+        assert np.all((c0 >= 0) & (c0 <= 1)) and c0.max() == 1.0
+        for a, f in enumerate(faces):
+            assert f.size == (n + 1) * n ** (r.dim - 1)
+        if r.dim == 2:
+            assert np.all(phi == 1.0)
+        else:
+            assert phi.min() >= 0.1 and phi.max() <= 0.3
+        # RT0 face fluxes of the separable field: zero net flux per cell
+        h = 1.0 / n
+        div = sum(np.diff(f, axis=r.dim - 1 - a) * h ** (r.dim - 1) for a, f in enumerate(faces))
+        assert np.abs(div).max() <= 1e-12 * max(np.abs(f).max() for f in faces)
+        t = (0.5) * r.dt
+        assert r.time_factor(0) == pytest.approx(r.amplitude * math.cos(math.pi * t / r.T), rel=1e-14)

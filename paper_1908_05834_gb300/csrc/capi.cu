@@ -579,11 +579,13 @@ bchar_status bchar_estimate_device_bytes(int dim, const int64_t *n_cells, const 
     }
     // bytes per cell, per ball and per matrix entry of every buffer a step holds:
     // mesh and row arrays 116, minimisation vectors 2 x 11 x 8, union-find 80,
-    // face velocities 12 d, row slab 12 row_cap, matching scratch 48, multigrid
-    // level 0 144 and coarser levels ~154; per entry: CSR and column view 68,
-    // multigrid level 0 48 and coarser ~50; per ball 8 + 4 (3 + 1) x precision.
+    // face velocities 12 d, tracking records kRecordLen x precision, row slab
+    // 12 row_cap, matching scratch 48, multigrid level 0 144 and coarser levels
+    // ~154; per entry: CSR and column view 68, multigrid level 0 48 and coarser
+    // ~50; per ball 8 + 4 (3 + 1) x precision.
     const int row_cap = dim == 2 ? 24 : 64;
-    const double per_cell = 116 + 176 + 80 + 12.0 * dim + 12.0 * row_cap + 48 + 144 + 154;
+    const double rec = kRecordLen * (o.precision == BCHAR_FP32_SPLIT ? 4.0 : 8.0);
+    const double per_cell = 116 + 176 + 80 + 12.0 * dim + rec + 12.0 * row_cap + 48 + 144 + 154;
     const double per_entry = 68 + 48 + 50;
     const double per_ball = 8 + 4.0 * (o.precision == BCHAR_FP32_SPLIT ? 4 : 8);
     const double nnz_bound = (dim == 2 ? 9.0 : 27.0) * nc;  // a 3^d neighbourhood per row

@@ -604,7 +604,7 @@ void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
         // restart the conjugate gradients from the true residual once it has
         // dropped by kInnerReduction: on these ill-conditioned systems short
         // cycles lose less to round-off than one long one
-        const double inner = fmax(kInnerReduction * kkt, 0.5 * target_abs);
+        const double inner = fmax(kInnerReduction * kkt, 0.75 * target_abs);
         cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
         k_copy<<<bl, kThreads, 0, s>>>(n2, F, res, nullptr);
         // FP32 V-cycle while the optimality residual is large, FP64 for the last digits

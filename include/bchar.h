@@ -100,6 +100,9 @@ typedef struct {
     int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
     int32_t amg_coarsest;    /* unknowns on its coarsest level */
     int32_t unbalanced;      /* connected components whose local targets were rescaled (see bchar_step) */
+    int32_t row_cap;         /* entries per row of the assembly's row slab: 24 (2D) or 64 (3D), grown to
+                              * the widest row (rounded up to 8) when a row did not fit; it never
+                              * shrinks, and the slab holds n_c x row_cap x 12 bytes */
     /* Milliseconds on the handle's stream (CUDA events) per stage of this call:
      * [0] tracking, [1] intersections and row assembly (with empty-column
      * seeding), [2] compaction, column view and target balancing, [3] the N

@@ -40,6 +40,7 @@ class StepInfo(ctypes.Structure):
                 ("refines", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
                 ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32),
+                ("row_cap", ctypes.c_int32),
                 ("ms_stage", ctypes.c_float * 8)]
 
     STAGES = ("track", "assemble", "columns_balance", "scaling", "minimise", "finalise", "update", "total")

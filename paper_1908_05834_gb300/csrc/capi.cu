@@ -497,6 +497,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->kernel_launches = m->launches;
         info->amg_levels = m->amg_levels;
         info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);
+        info->row_cap = m->row_cap;
         info->unbalanced = h->unbalanced;
         for (int k = 0; k < 8; ++k) info->ms_stage[k] = ms_stage[k];
     }

@@ -62,3 +62,33 @@ def test_footprint_estimate_on_the_host():
         bchar.estimate_device_bytes(u, bchar.default_options(qp_warm_start=2))
     with pytest.raises(bchar.BcharError):
         bchar.estimate_device_bytes([np.array([0.0, 0.5, 0.5, 1.0])] * 2)  # a zero width
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of bchar_options and bchar_step_info have the
+    header's field names, offsets and sizes (a C program compiled against
+    include/bchar.h prints them); bchar_step_batch indexes an array of
+    bchar_step_info, so a size mismatch would shift every instance's info."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1908_05834_gb300 import bchar
+    pairs = (("bchar_options", bchar.Options), ("bchar_step_info", bchar.StepInfo))
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "bchar.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for cname, cls in pairs:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -246,9 +246,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded analytic fields and meshes)",
-        "config": {"workload": f"{WORKLOAD}: 1024x1024 stretched tensor mesh (widths U[0.5h,1.5h], seed 1001), "
-                                "phi=1, single vortex x cos(pi t/T), T=1, dt=0.005, disk c0; FP32 tracking and "
-                                "intersections, FP64 sums/scalings/minimisation/update",
+        "config": {"workload": f"{args.workload}: {inputs.describe(args.workload, args.n)}",
                    "cells": nc, "cells_per_axis": len(wl.coords[0]) - 1, "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps",
                    "qp_tol": args.qp_tol, "qp_max_iter": args.qp_max_iter,
                    "qp_note": "the minimisation is solved to qp_tol (relative L1 optimality residual); global mass "

@@ -207,6 +207,24 @@ def workload(name: str, n: int | None = None, steps: int | None = None) -> Workl
 
 WORKLOADS = ("vortex2d_32", "vortex2d_1024", "deform3d_128", "deform3d_256")
 
+_SPLIT = "FP32 tracking and intersections, FP64 sums/scalings/minimisation/update"
+_RECIPES = {
+    "vortex2d_32": (32, "uniform {n}x{n} mesh, phi=1, steady single vortex, dt=0.01, disk c0; FP64 throughout"),
+    "vortex2d_1024": (1024, "{n}x{n} stretched tensor mesh (widths U[0.5h,1.5h], seed 1001), phi=1, single vortex "
+                            "x cos(pi t/T), T=1, dt=0.005, disk c0; " + _SPLIT),
+    "deform3d_128": (128, "uniform {n}^3 mesh, phi log-U[0.1,0.3] (seed 2002), deformation field x cos(pi t/T), "
+                          "T=1.5, dt=0.01, ball c0; " + _SPLIT),
+    "deform3d_256": (256, "{n}^3 stretched tensor mesh (widths U[0.7h,1.3h], seed 3001), phi log-U[0.05,0.3] "
+                          "(seed 3002), deformation field x cos(pi t/T), T=1.5, dt=0.005, Gaussian c0 stored in "
+                          "FP32; " + _SPLIT),
+}
+
+
+def describe(name: str, n: int | None = None) -> str:
+    """One line naming a workload's recipe and size (for measurement records)."""
+    default, text = _RECIPES[name]
+    return text.format(n=n or default)
+
 
 # ---------------------------------------------------------------- serving stream
 

@@ -143,3 +143,24 @@ def test_serving_request_payloads():
         assert np.abs(div).max() <= 1e-12 * max(np.abs(f).max() for f in faces)
         t = (0.5) * r.dt
         assert r.time_factor(0) == pytest.approx(r.amplitude * math.cos(math.pi * t / r.T), rel=1e-14)
+
+
+@pytest.mark.parametrize("name", ["vortex2d_32", "vortex2d_1024", "deform3d_128", "deform3d_256"])
+def test_workload_descriptions_follow_the_recipes(name):
+    """The one-line description a measurement records names the recipe the
+    workload actually builds: its size, time step, storage and precision."""
+    import numpy as np
+    from paper_1908_05834_gb300 import inputs
+    assert name in inputs.WORKLOADS
+    n = 6
+    wl = inputs.workload(name, n=n)
+    text = inputs.describe(name, n)
+    size = f"{n}x{n}" if wl.dim == 2 else f"{n}^3"
+    assert text.startswith(size) or text.startswith(f"uniform {size}")
+    assert f"dt={wl.dt:g}" in text
+    assert ("stored in FP32" in text) == (wl.c_dtype == "f32")
+    assert ("FP32 tracking" in text) == (wl.precision == "fp32split")
+    assert ("stretched" in text) == (len(set(np.round(np.diff(wl.coords[0]), 12))) > 1)
+    assert ("steady" in text) == (wl.T is None)
+    d = int(name.split("_")[1])  # the default size is in the name
+    assert (f"{d}x{d}" if wl.dim == 2 else f"{d}^3") in inputs.describe(name)

@@ -387,6 +387,7 @@ def run_served(args, torch, bchar, inputs):
               "peak_admitted_gb": round(srv.peak_used / 1e9, 2), "peak_active": srv.peak_active,
               "max_peak_bytes_over_estimate": round(max((r.peak_bytes / r.est_bytes) for r in res
                                                         if r.status == "ok"), 3),
+              "footprint_overruns": len(srv.overruns),  # requests charged above their estimate
               "prep_s": round(prep_s, 1),
               "sample": f"first {len(reqs)} of the 512-request serving stream (seed 4004), full step counts, "
                         f"FP32 split, qp_tol {args.qp_tol}"})

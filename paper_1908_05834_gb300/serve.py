@@ -14,6 +14,11 @@ when it has arrived, fewer than ``max_active`` requests run, and its device
 footprint estimate (``bchar_estimate_device_bytes``) fits in what is left of
 the memory budget; later requests wait behind it (no overtaking, so no
 starvation).  A request whose estimate exceeds the whole budget is rejected.
+A running request reports the device memory it holds after every step; when
+that exceeds its estimate (a step whose rows outgrow the row slab's initial
+width holds more than the estimate), the larger figure is charged against the
+budget from then on, so later admissions wait instead of over-committing the
+device.
 
 Every step runs in the library's kernels (``bchar.Mesh.step``); this module
 only schedules.  The scheduler itself takes the executor and the estimator as
@@ -53,9 +58,11 @@ class Server:
     """First-come first-served admission under a device-memory budget and a
     limit on concurrent requests; one host thread per running request.
 
-    executor(request) -> dict with at least "c" (final concentration, host) and
-    optionally "peak_bytes"; it may raise, which fails that request only.
-    estimator(request) -> int bytes.  clock() -> seconds."""
+    executor(request, report) -> dict with at least "c" (final concentration,
+    host) and optionally "peak_bytes"; it may raise, which fails that request
+    only.  report(bytes) may be called any number of times while it runs, with
+    the device memory the request holds.  estimator(request) -> int bytes.
+    clock() -> seconds."""
 
     def __init__(self, executor: Callable[[Any], dict], estimator: Callable[[Any], int],
                  budget_bytes: float = 120e9, max_active: int = 32, clock: Callable[[], float] = time.perf_counter):
@@ -69,27 +76,41 @@ class Server:
         self.peak_used = 0.0          # largest sum of admitted estimates
         self.peak_active = 0
         self.admission_log: list[tuple[float, int, float]] = []  # (time, rid, bytes in use after admission)
+        self.overruns: list[tuple[float, int, int, int]] = []     # (time, rid, estimate, reported bytes)
 
     def run(self, requests) -> list[Result]:
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival_s, r.rid)))
         cond = threading.Condition()
         results: dict[int, Result] = {}
         active: dict[int, threading.Thread] = {}
+        charged: dict[int, float] = {}  # bytes each running request holds against the budget
         used = [0.0]
         t0 = self.clock()
 
         def now() -> float:
             return self.clock() - t0
 
+        def reporter(rid, est):
+            def report(nbytes):
+                with cond:
+                    extra = float(nbytes) - charged[rid]
+                    if extra > 0:
+                        if charged[rid] == est:
+                            self.overruns.append((now(), rid, est, int(nbytes)))
+                        charged[rid] = float(nbytes)
+                        used[0] += extra
+                        self.peak_used = max(self.peak_used, used[0])
+            return report
+
         def worker(req, est, admitted):
             try:
-                out = self.executor(req)
+                out = self.executor(req, reporter(req.rid, est))
                 res = Result(req.rid, req.arrival_s, admitted, now(), req.nc, req.steps, est, "ok", out.get("c"),
                              int(out.get("peak_bytes", 0)), {k: v for k, v in out.items() if k not in ("c",)})
             except Exception as e:  # the request fails, the server goes on
                 res = Result(req.rid, req.arrival_s, admitted, now(), req.nc, req.steps, est, f"error: {e}")
             with cond:
-                used[0] -= est
+                used[0] -= charged.pop(req.rid)
                 del active[req.rid]
                 results[req.rid] = res
                 cond.notify_all()
@@ -112,6 +133,7 @@ class Server:
                         break
                     pending.popleft()
                     used[0] += est
+                    charged[req.rid] = float(est)
                     self.peak_used = max(self.peak_used, used[0])
                     self.admission_log.append((t, req.rid, used[0]))
                     th = threading.Thread(target=worker, args=(req, est, t), daemon=True)
@@ -165,7 +187,7 @@ class GpuExecutor:
         self.options = options
         self.device = device
 
-    def __call__(self, req) -> dict:
+    def __call__(self, req, report=None) -> dict:
         import torch
         from . import bchar
         torch.cuda.set_device(self.device)
@@ -186,6 +208,8 @@ class GpuExecutor:
                     for name, ms in info["ms_stage"].items():
                         stage_ms[name] = stage_ms.get(name, 0.0) + ms
                     c, out = out, c
+                    if report is not None:
+                        report(mesh.device_bytes()[1])
                 host = c.cpu().numpy()
                 peak = mesh.device_bytes()[1]
             finally:

@@ -19,12 +19,15 @@ class Req:
     steps: int = 1
     work_s: float = 0.02
     fail: bool = False
+    report_bytes: int | None = None  # device memory the request reports once it runs
 
 
 def fake_executor(running: list, lock: threading.Lock):
-    def run(req):
+    def run(req, report):
         with lock:
             running.append(req.rid)
+        if req.report_bytes is not None:
+            report(req.report_bytes)
         time.sleep(req.work_s)
         with lock:
             running.remove(req.rid)
@@ -84,6 +87,27 @@ def test_oversize_rejected_and_failure_isolated():
     assert res[0].status.startswith("rejected")
     assert res[1].status.startswith("error") and "planted" in res[1].status
     assert res[2].status == "ok"
+
+
+def test_reported_footprint_above_the_estimate_delays_admission():
+    # request 0 is estimated at 30 but holds 90 once it runs: request 1 (30)
+    # would fit beside the estimate (60 <= 100) but not beside the 90
+    reqs = [Req(0, 0.0, 30, work_s=0.25, report_bytes=90), Req(1, 0.05, 30, work_s=0.0)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=100, max_active=4)
+    res = srv.run(reqs)
+    assert all(r.status == "ok" for r in res)
+    assert res[1].admitted_s >= res[0].finished_s - 1e-3
+    assert [(rid, est, got) for _, rid, est, got in srv.overruns] == [(0, 30, 90)]
+    assert srv.peak_used == 90
+
+
+def test_reported_footprint_below_the_estimate_keeps_the_estimate():
+    # the estimate stays charged when a request reports less (it may still grow)
+    reqs = [Req(0, 0.0, 30, work_s=0.25, report_bytes=10), Req(1, 0.05, 40, work_s=0.0)]
+    srv = serve.Server(fake_executor([], threading.Lock()), by_cells, budget_bytes=60, max_active=4)
+    res = srv.run(reqs)
+    assert res[1].admitted_s >= res[0].finished_s - 1e-3
+    assert srv.overruns == [] and srv.peak_used == 40
 
 
 def test_waits_for_arrivals():

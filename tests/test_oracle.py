@@ -231,6 +231,17 @@ def test_whole_cell_translation_is_a_shift():
         row = A0.getrow(k)
         assert row.nnz == 1 and row.indices[0] == k - 1
         assert row.data[0] == pytest.approx(h * h, rel=1e-12)
+    # the seeds (reading of the empty columns): the centre of an empty cell M_j
+    # carried forward over dt leaves through the right wall and is clamped into
+    # M_j itself, so row j gains a_jj = |M_j|_phi exactly, the only entry of
+    # column j, on top of its own transfer to the cell on its left
+    Ac = A0.tocsc()
+    for j in range(n - 1, mesh.nc, n):
+        col = Ac.getcol(j)
+        assert col.nnz == 1 and col.indices[0] == j and col.data[0] == mesh.volphi()[j]
+        row = A0.getrow(j)
+        assert sorted(row.indices) == [j - 1, j]
+        assert row.sum() == pytest.approx(2 * mesh.volphi()[j], rel=1e-12)
 
 
 def test_initial_matrix_matches_brute_force():

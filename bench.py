@@ -260,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
                        "qp_converged": sum(i["qp_converged"] for i in infos),
                        "kkt_rel_max": max(i["kkt_rel"] for i in infos),
                        "max_rel_row_res_max": max(i["max_rel_row_res"] for i in infos),
-                       "amg_levels": last["amg_levels"], "nnz": last["nnz"],
+                       "amg_levels": last["amg_levels"], "amg_coarsest": last["amg_coarsest"], "nnz": last["nnz"],
+                       "row_cap": last["row_cap"],
                        "substeps": last["substeps"],
                        "max_rel_mass_change": max(abs(i["mass_after"] - i["mass_before"]) / i["mass_before"]
                                                   for i in infos)},

@@ -255,8 +255,9 @@ bchar_status bchar_device_bytes(bchar_mesh_t m, int64_t *now, int64_t *peak);
  * multigrid), per ball (the tight packing, counted here from the widths)
  * and per matrix entry, with the entries bounded by a 3^d neighbourhood per
  * row (9 in 2D, 27 in 3D), plus 10 %.  A step whose rows grow wider than the
- * slab's initial capacity (24 entries in 2D, 64 in 3D) holds more.  Host
- * only; no GPU work.  coords as for bchar_create_mesh; opt NULL = defaults.
+ * slab's initial capacity (24 entries in 2D, 64 in 3D) holds more: about
+ * n_c x 12 x (row_cap - initial capacity) bytes, with row_cap as reported in
+ * bchar_step_info.  Host only; no GPU work.  coords as for bchar_create_mesh; opt NULL = defaults.
  * Errors: INVALID_ARG. */
 bchar_status bchar_estimate_device_bytes(int dim, const int64_t n_cells[3], const double *const coords[3],
                                          const bchar_options *opt, int64_t *bytes);

@@ -1,6 +1,7 @@
 """Host-side rules of the serving loop (no GPU): first-come first-served
 admission, the memory budget, the limit on running requests, rejection and
 failure isolation.  The executor is a fake that sleeps."""
+import sys
 import threading
 import time
 from dataclasses import dataclass
@@ -188,3 +189,61 @@ def test_workload_descriptions_follow_the_recipes(name):
     assert ("steady" in text) == (wl.T is None)
     d = int(name.split("_")[1])  # the default size is in the name
     assert (f"{d}x{d}" if wl.dim == 2 else f"{d}^3") in inputs.describe(name)
+
+
+def test_gpu_executor_host_logic_with_a_fake_mesh(monkeypatch):
+    """GpuExecutor's bookkeeping without a GPU: one report per step of the
+    handle's device bytes (charged by the server above the estimate), the CG
+    iterations and stage times summed over the steps, the peak returned, the
+    final c copied back.  The CUDA calls and the mesh are replaced by fakes."""
+    import contextlib
+    import types
+
+    import numpy as np
+    import torch
+
+    from paper_1908_05834_gb300 import inputs
+
+    class FakeStream:
+        cuda_stream = 0
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    to = torch.Tensor.to
+    # a device copy: a new tensor, like a real upload
+    monkeypatch.setattr(torch.Tensor, "to", lambda self, *a, **k: self.clone() if a[:1] == ("cuda",) else to(self, *a, **k))
+
+    class FakeMesh:
+        def __init__(self, coords, phi, opts, stream=None):
+            self.bytes = 100
+
+        def set_velocity(self, faces, scale=1.0):
+            pass
+
+        def step(self, dt, c, out):
+            out.copy_(c * 0.5)
+            self.bytes += 50
+            return {"cg_iters": 3, "ms_stage": {"total": 1.5}}
+
+        def device_bytes(self):
+            return self.bytes, self.bytes
+
+        def close(self):
+            pass
+
+    fake = types.SimpleNamespace(Mesh=FakeMesh, estimate_device_bytes=lambda coords, opts: 120)
+    import paper_1908_05834_gb300 as pkg
+    monkeypatch.setitem(sys.modules, "paper_1908_05834_gb300.bchar", fake)
+    monkeypatch.setattr(pkg, "bchar", fake, raising=False)
+
+    req = inputs.ServeRequest(rid=0, arrival_s=0.0, dim=2, n=16, amplitude=1.0, cfl=1.0, steps=3, phi_seed=1)
+    prepared = {0: req.materialize()}
+    srv = serve.Server(serve.GpuExecutor(prepared, None), serve.estimator_for(prepared, None),
+                       budget_bytes=1e9, max_active=2)
+    (res,) = srv.run([req])
+    assert res.status == "ok" and res.est_bytes == 120 and res.peak_bytes == 250
+    assert res.extra["cg_iters"] == 9 and res.extra["stage_ms"] == {"total": 4.5}
+    assert np.allclose(res.c, prepared[0][3] * 0.125)
+    assert [(rid, est, got) for _, rid, est, got in srv.overruns] == [(0, 120, 150)]
+    assert srv.peak_used == 250

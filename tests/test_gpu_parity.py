@@ -246,6 +246,13 @@ def test_full_size_sampled_rows(bc, name, precision):
     rows of A^(0) recomputed one by one by the oracle, plus invariants.  The
     256^3 workload keeps c in FP32 (its stored mass is checked too); its
     matrix is read row by row from the exported arrays (no sparse copy)."""
+    if name == "deform3d_256":
+        # one step holds about 264 GB while a row wider than the slab makes the
+        # slab that wide for every row (measured on a 284 GB device)
+        import torch
+        free, _ = torch.cuda.mem_get_info()
+        if free < 270e9:
+            pytest.skip(f"needs about 270 GB of free device memory, {free / 1e9:.0f} GB free")
     wl = inputs.workload(name)
     faces = wl.faces(0)
     c = wl.c0 if wl.c_dtype == "f32" else wl.c0.astype(np.float64)

@@ -14,13 +14,15 @@ the paper's order and notation, in double precision:
 * initial weights V_{K,M}                   (Sec 3.1, eq. fracMaterial, eq. ball_int)
 * consistent local targets per component    (Sec 3.2, eq. localmassconsMat / globalmassconsMat)
 * alternating column/row scaling, N times   (Sec 3.2, eq. volAdj)
-* the matrix A-hat and the minimisation     (Sec 3.2, eq. opti_masscons)
+* the matrix A-hat and the bound-constrained
+  minimisation, 0 <= 1 + x <= 2 inside it   (Sec 3.2, eq. opti_masscons)
 * a final column scaling                    (Sec 3.2, first half of eq. volAdj)
 * the update |K|_phi c_K^{n+1} = sum_M a_KM c_M^n (Sec 2, eq. phys-inter-ELLAM)
 
 The per-ball loops (tracking, intersections) are plain C in
 ``bchar_oracle.c``; the matrix steps use numpy / scipy.sparse, with a sparse
-direct solve (SuperLU) as the linear-algebra primitive of the minimisation.
+direct solve (SuperLU) as the linear-algebra primitive of every interior-point
+iteration of the minimisation.
 """
 from __future__ import annotations
 
@@ -344,27 +346,22 @@ def initial_matrix(mesh: Mesh, faces, dt: float, substeps: int, drop_tol: float 
     return A0, {"void_balls": voids, "empty_cols": n_empty, "ball_offset": offset, "centres": centres, "rhat": rhat}
 
 
-def balanced_targets(A0: sp.csr_matrix, volphi: np.ndarray, tol: float = 1e-12, theta: float = 1e-3):
+def balanced_targets(A0: sp.csr_matrix, volphi: np.ndarray, tol: float = 1e-12):
     """Local targets made consistent with the global ones (reading).
 
     eq. localmassconsMat and eq. globalmassconsMat can hold together only if,
-    on every connected block of rows and columns, the sum of |K_i|_phi over
-    its rows equals the sum of |M_j|_phi over its columns.  The balls can
-    break this on stretched or porous meshes.  Blocks are the connected
-    components of the graph linking row i to column j when
-    a_ij >= theta * max(largest entry of row i, largest entry of column j):
-    a sliver overlap below that share cannot carry a block's mismatch (it
-    would need 1 + x far outside the bounds 0 <= 1 + x <= 2).  On a block with
-    relative mismatch > tol the row targets are multiplied by
-    sum_cols / sum_rows: global mass conservation stays exact and local
-    conservation is relaxed by that factor there only.
-    Returns (b_loc, number of rescaled blocks)."""
+    on every connected component of the pattern of A (row i linked to column
+    j whenever a_ij != 0), the sum of |K_i|_phi over its rows equals the sum of
+    |M_j|_phi over its columns: both sums equal the sum of the component's
+    entries once the constraints hold.  Where a component breaks this by more
+    than tol (relative), its row targets are multiplied by sum_cols / sum_rows,
+    so global mass conservation stays exact and local conservation is relaxed
+    by that factor on that component only.  Returns (b_loc, number of rescaled
+    components)."""
     n = A0.shape[0]
     rows = np.repeat(np.arange(n), np.diff(A0.indptr))
-    rowmax = np.asarray(A0.max(axis=1).todense()).reshape(-1)
-    colmax = np.asarray(A0.max(axis=0).todense()).reshape(-1)
-    strong = A0.data >= theta * np.maximum(rowmax[rows], colmax[A0.indices])
-    G = sp.csr_matrix((np.ones(int(strong.sum())), (rows[strong], A0.indices[strong] + n)), shape=(2 * n, 2 * n))
+    nz = A0.data != 0.0
+    G = sp.csr_matrix((np.ones(int(nz.sum())), (rows[nz], A0.indices[nz] + n)), shape=(2 * n, 2 * n))
     ncomp, labels = csgraph.connected_components(G, directed=False)
     sum_rows = np.zeros(ncomp)
     sum_cols = np.zeros(ncomp)
@@ -421,57 +418,106 @@ def hat_matrix(AN: sp.csr_matrix) -> sp.csr_matrix:
     return sp.vstack([top, bottom]).tocsr()
 
 
-def minimise(AN: sp.csr_matrix, row_target, col_target, tol: float = 1e-14, penalty: float = 1e-7,
-             max_refine: int = 30):
-    """The mass-conservation minimisation of Sec 3.2 (eq. opti_masscons).
+def minimise(AN: sp.csr_matrix, row_target, col_target, tol: float = 1e-12, penalty: float = 1e-7,
+             max_iter: int = 200):
+    """The mass-conservation minimisation of Sec 3.2 (eq. opti_masscons), with
+    the paper's bounds 0 <= 1 + x <= 2 enforced inside it.
 
-    The paper minimises x^T x over x in R^{n_z} subject to A-hat (1 + x) = b
+    The paper minimises x.x over x in R^{n_z} subject to A-hat (1 + x) = b
     (row sums |K_i|_phi, eq. localmassconsMat; column sums |M_j|_phi,
-    eq. globalmassconsMat) and 0 <= 1 + x <= 2.  With balls this problem can
-    have no solution at all (the constraints can disagree on a connected
-    block of cells, and the bounds can conflict with them), so the reading
-    used throughout is:
+    eq. globalmassconsMat) and the bounds.  The reading used throughout:
+    the bounds are hard (closed: the open bound 0 < 1 + x has no minimiser)
+    and the 2 n_c mass constraints are enforced by a quadratic penalty,
 
-      1. x minimises 1/2 x.x + 1/2 sum_l (s_l / (eps b_l))^2 over R^{n_z},
-         s = b - A-hat (1 + x) the 2 n_c constraint residuals and
-         eps = penalty: a unique, always defined penalised minimum-norm
-         adjustment, which tends to the paper's minimiser as eps -> 0
-         whenever that one lies inside the bounds;
-      2. the bounds are applied: 1 + x is clipped to [0, 2];
-      3. (``column_fix``) every column is scaled to its target, so global mass
-         conservation holds to rounding.
+        minimise  1/2 x.x + 1/(2 eps^2) sum_l (s_l / b_l)^2
+        over      0 <= 1 + x <= 2,     s = b - A-hat (1 + x),  eps = penalty,
 
-    Step 1 is the linear system (A-hat A-hat^T + diag(w)) y = r,
-    w = (eps b)^2, r = b - A-hat 1, x = A-hat^T y, solved by SuperLU with
-    iterative refinement.  x is accumulated per entry next to y: y can grow
-    very large along weak (near-tangent) entries and y_i + y_j would cancel
-    away the digits of x.  Refinement stops when the L1 norm of
-    r - A-hat x - w y is <= tol * sum(b_loc).
+    which has exactly one minimiser for every input.  Where the paper's
+    problem has a solution this minimiser tends to it as eps -> 0, with
+    constraint residuals s_l = eps^2 b_l^2 y_l (y the multipliers of the
+    constraints); where it has none (the bounds and the constraints cannot
+    all hold), it is the adjustment within the bounds with the least relative
+    constraint violation in the least-squares sense, then the least x.x.
 
-    Returns (1 + x clipped to [0, 2], x, info)."""
+    Solved by a primal-dual interior-point method (Mehrotra's predictor-
+    corrector), written out for this problem with f = 1 + x, the constraints
+    divided by their targets (G = diag(b)^-1 A-hat, so every target is 1) and
+    the upper bound carried by its own slack u = 2 - f (f near 2 would lose
+    u to rounding):
+        stationarity  f - 1 - G^T y - zeta_lo + zeta_hi = 0
+        constraints   G f + eps^2 y = 1
+        bounds        f, u, zeta_lo, zeta_hi >= 0 with f zeta_lo = u zeta_hi = mu -> 0.
+    Every iteration solves the normal equations (G D G^T + eps^2 I) dy = r,
+    D = 1 / (1 + zeta_lo / f + zeta_hi / u) per entry, twice (predictor and
+    corrector) with one sparse factorisation (SuperLU, the linear-algebra
+    primitive), and steps 0.99 of the way to the boundary.  It stops when the
+    scaled constraint residual is <= tol, mu <= 1e-15 and the stationarity
+    residual is <= 1e-12 of the largest dual value (y grows to ~1e12 where the
+    problem is infeasible, and G^T y then carries that much rounding; the
+    entries of G are at most 1).
+
+    Returns (f = 1 + x in [0, 2], x, info); info has the iteration count, the
+    final scaled constraint residual, converged, the number of entries within
+    1e-9 of a bound, and the dual y of the unscaled constraints."""
     H = hat_matrix(AN)
-    HT = H.T.tocsr()
     b = np.concatenate([row_target, col_target])
-    r = b - np.asarray(H.sum(axis=1)).reshape(-1)
-    w = (penalty * b) ** 2
-    scale_ = float(np.sum(row_target))
-    lu = spla.splu((H @ HT + sp.diags(w)).tocsc(), permc_spec="COLAMD")
-    x = np.zeros(H.shape[1])
-    y = np.zeros(H.shape[0])
-    refines = 0
-    kkt = float("inf")
-    for _ in range(max_refine):
-        F = r - H @ x - w * y
-        kkt = float(np.sum(np.abs(F)))
-        if kkt <= tol * scale_:
+    G = (sp.diags(1.0 / b) @ H).tocsr()
+    GT = G.T.tocsr()
+    m, nz = G.shape
+    w = penalty * penalty
+    f = np.ones(nz)
+    u = np.ones(nz)
+    zlo = np.ones(nz)
+    zhi = np.ones(nz)
+    y = np.zeros(m)
+    one = np.ones(m)
+    converged = False
+    it = 0
+    rp = one.copy()
+
+    def to_boundary(v, dv):
+        neg = dv < 0.0
+        return min(1.0, float(np.min(-v[neg] / dv[neg]))) if neg.any() else 1.0
+
+    for it in range(max_iter + 1):
+        rd = (f - 1.0) - GT @ y - zlo + zhi
+        rp = one - G @ f - w * y
+        ru = 2.0 - f - u
+        mu = float(f @ zlo + u @ zhi) / (2 * nz)
+        dual_scale = 1.0 + max(float(np.max(np.abs(y))), float(zlo.max()), float(zhi.max()))
+        if np.max(np.abs(rp)) <= tol and mu <= 1e-15 and np.max(np.abs(rd)) <= 1e-12 * dual_scale:
+            converged = True
             break
-        d = lu.solve(F)
-        x = x + HT @ d
-        y = y + d
-        refines += 1
-    factor = np.clip(1.0 + x, 0.0, 2.0)
-    info = {"refines": refines, "kkt_l1": kkt, "n_clipped": int(np.sum((1.0 + x < 0.0) | (1.0 + x > 2.0)))}
-    return factor, x, info
+        if it == max_iter:
+            break
+        D = 1.0 / (1.0 + zlo / f + zhi / u)
+        lu = spla.splu((G @ sp.diags(D) @ GT + w * sp.eye(m)).tocsc(), permc_spec="COLAMD")
+
+        def direction(c_lo, c_hi):
+            # linearised: zeta_lo df + f dzeta_lo = c_lo, zeta_hi du + u dzeta_hi = c_hi, du = ru - df
+            q = -rd + c_lo / f - c_hi / u + (zhi / u) * ru
+            dy = lu.solve(rp - G @ (D * q))
+            df = D * (q + GT @ dy)
+            du = ru - df
+            return df, du, dy, (c_lo - zlo * df) / f, (c_hi - zhi * du) / u
+
+        df, du, dy, dzlo, dzhi = direction(-f * zlo, -u * zhi)  # predictor (affine scaling)
+        ap = min(to_boundary(f, df), to_boundary(u, du))
+        ad = min(to_boundary(zlo, dzlo), to_boundary(zhi, dzhi))
+        mu_aff = float((f + ap * df) @ (zlo + ad * dzlo) + (u + ap * du) @ (zhi + ad * dzhi)) / (2 * nz)
+        sigma = min(1.0, (mu_aff / mu) ** 3)
+        df, du, dy, dzlo, dzhi = direction(sigma * mu - f * zlo - df * dzlo, sigma * mu - u * zhi - du * dzhi)
+        ap = 0.99 * min(to_boundary(f, df), to_boundary(u, du))
+        ad = 0.99 * min(to_boundary(zlo, dzlo), to_boundary(zhi, dzhi))
+        f = f + ap * df
+        u = u + ap * du
+        y = y + ad * dy
+        zlo = zlo + ad * dzlo
+        zhi = zhi + ad * dzhi
+    f = np.clip(f, 0.0, 2.0)
+    info = {"iterations": it, "kkt_l1": float(np.max(np.abs(rp))), "converged": converged,
+            "n_at_bounds": int(np.sum((f < 1e-9) | (f > 2.0 - 1e-9))), "y": y / b}
+    return f, f - 1.0, info
 
 
 def column_fix(Aq: sp.csr_matrix, AN: sp.csr_matrix, col_target) -> sp.csr_matrix:
@@ -506,7 +552,7 @@ def total_mass(mesh: Mesh, c) -> float:
 @dataclass
 class StepOptions:
     n_scale: int = 10          # N of Algorithm 1 (Sec 4: N = 10)
-    qp_tol: float = 1e-14
+    qp_tol: float = 1e-12      # scaled constraint residual at which the minimisation stops
     penalty: float = 1e-7      # eps of the constraint penalty in ``minimise``
     drop_tol: float = 1e-12
     cfl: float = 0.5

@@ -18,8 +18,7 @@
  *   - ball-ball intersection measure (lens area / lens volume)  (Sec 3, "trivial" intersections)
  *   - the initial weights V_{K,M}                               (Sec 3.1, eq. fracMaterial, eq. ball_int)
  *
- * Readings where the paper is silent (each one is listed with its reason in
- * the design notes of the repository):
+ * Readings where the paper is silent:
  *   - all balls of a cell have the radius r_K = min(width)/(2 nb) (a quarter of
  *     the smallest face for nb = 2); along axis a the cell holds
  *     n_a = max(nb, floor(nb w_a / w_min)) balls at the centres of an equal

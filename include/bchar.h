@@ -63,21 +63,17 @@ typedef struct {
     int substeps;       /* RK4 substeps per step; 0 = smallest s with dt*vmax/s <= cfl*hmin */
     double cfl;         /* 0.5 */
     double drop_tol;    /* entries V_KM < drop_tol |K|_phi are dropped (1e-12) */
-    double penalty;     /* eps of the penalised minimisation (1e-7), see bchar_step */
-    double qp_tol;      /* stop when the L1 optimality residual <= qp_tol * sum |K|_phi (1e-14);
-                           the iterations stop at a floor of about 1e-9..1e-11 (rounding in the
-                           near-null directions of the dual), so a smaller qp_tol ends at the
-                           floor, with qp_converged = 0 in bchar_step_info */
-    int qp_max_iter;    /* cap on conjugate-gradient iterations per solve (200000) */
-    int qp_max_refine;  /* cap on refinement rounds (60) */
+    double penalty;     /* eps of the elastic penalty of the minimisation (1e-7), see bchar_step */
+    double qp_tol;      /* the minimisation stops when every constraint residual is <= qp_tol of
+                           its target (1e-9), the mean complementarity is <= 1e-12 and the
+                           stationarity residuals are <= 1e-12 of the largest multiplier */
+    int qp_max_iter;    /* cap on conjugate-gradient iterations of one step, all solves (200000) */
+    int qp_max_refine;  /* cap on interior-point iterations of one step (100) */
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
     int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
                            1 = aggregation multigrid (default), 0 = Jacobi */
-    int qp_warm_start;  /* 1 (default): start the minimisation from the dual of the handle's
-                           previous step (the rows and columns are the same cells, and the
-                           dual changes little between steps: 30-60 % fewer iterations),
-                           except every 32nd step, which starts from zero; 0: always start
-                           from zero.  The result meets qp_tol either way. */
+    int qp_warm_start;  /* reserved (0 or 1, default 1): every minimisation starts from
+                           1 + x = 1 with unit bound multipliers and zero constraint multipliers */
 } bchar_options;
 
 typedef struct {
@@ -87,15 +83,15 @@ typedef struct {
     double max_rel_row_res;  /* max_K |sum_M a_KM - |K|_phi| / |K|_phi  (eq. localmassconsMat) */
     double max_rel_col_res;  /* max_M |sum_K a_KM - |M|_phi| / |M|_phi  (eq. globalmassconsMat) */
     double scale_err;        /* max relative column error after the N scalings */
-    double kkt_rel;          /* final L1 optimality residual / sum |K|_phi of the minimisation */
+    double kkt_rel;          /* largest constraint residual / target of the minimisation's result */
     int64_t nnz;             /* non-zeros of A */
     int32_t substeps;        /* RK4 substeps used */
-    int32_t cg_iters;        /* conjugate-gradient iterations, all refinement rounds */
-    int32_t refines;         /* refinement rounds of the minimisation */
-    int32_t qp_converged;    /* 1 if kkt_rel <= qp_tol */
+    int32_t cg_iters;        /* conjugate-gradient iterations, all solves of the minimisation */
+    int32_t ip_iters;        /* interior-point iterations of the minimisation */
+    int32_t qp_converged;    /* 1 if the minimisation met its stopping rule (see qp_tol) */
     int32_t void_balls;      /* tracked balls that met no residing ball */
     int32_t empty_cols;      /* residing cells no tracked ball reached (seeded) */
-    int32_t n_clipped;       /* entries whose 1 + x left [0, 2] */
+    int32_t n_at_bounds;     /* entries whose 1 + x ends within 1e-9 of 0 or 2 */
     int32_t kernel_launches; /* kernels launched by this call */
     int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
     int32_t amg_coarsest;    /* unknowns on its coarsest level */
@@ -147,16 +143,23 @@ bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int
  *      classical RK4 (Sec 2 eq. charac, Sec 3 eq. rTrackedBall);
  *   2. a^(0)_KM = V_{K,M} from the closed-form ball intersections
  *      (Sec 3.1, eq. fracMaterial, eq. ball_int);
- *   3. consistent targets: on a connected component of A's pattern whose
- *      local targets sum_rows |K_i|_phi differ from its global ones
- *      sum_cols |M_j|_phi (the balls can cause this), the local targets are
- *      scaled by their ratio; then N alternating column/row scalings
- *      (Sec 3.2, eq. volAdj);
- *   4. the minimisation of Sec 3.2 (eq. opti_masscons), read as: the
- *      penalised minimum-norm adjustment x of min 1/2 x.x + 1/2 sum (s/(eps b))^2
- *      (s the 2 n_c constraint residuals), then 1 + x clipped to the paper's
- *      bounds [0, 2], then every column scaled to |M|_phi so that global mass
- *      is conserved to rounding;
+ *   3. consistent targets: on a connected component of A's pattern (row i
+ *      and column j linked by every non-zero a_ij) whose local targets
+ *      sum_rows |K_i|_phi differ from its global ones sum_cols |M_j|_phi (the
+ *      balls can cause this), the local targets are scaled by their ratio;
+ *      then N alternating column/row scalings (Sec 3.2, eq. volAdj);
+ *   4. the minimisation of Sec 3.2 (eq. opti_masscons) with the paper's bounds
+ *      0 <= 1 + x <= 2 inside it, read as: minimise 1/2 x.x + sum_l h(v_l) over
+ *      the bounds, v_l the relative violation of each of the 2 n_c mass
+ *      constraints and h quadratic (v^2 / (2 eps^2), eps = penalty) up to
+ *      |v| = 1e-6 and linear beyond.  Where the paper's problem has a solution
+ *      this is that solution up to residuals eps^2 y_l; where the balls make
+ *      the constraints contradictory (a cell whose only tracked overlap is a
+ *      smaller neighbour), the total relative violation is the least the
+ *      bounds allow.  Solved by a primal-dual interior-point method whose
+ *      linear systems are solved by multigrid-preconditioned conjugate
+ *      gradients; then every column scaled to |M|_phi so that global mass is
+ *      conserved to rounding;
  *   5. c_out = W c_in (eq. phys-inter-ELLAM), FP64 accumulation.
  * c_in, c_out: DEVICE arrays of n_c values of type c_dtype, caller-owned, not
  * aliased.  info: optional (NULL), written on return.  The call returns when

@@ -419,104 +419,123 @@ def hat_matrix(AN: sp.csr_matrix) -> sp.csr_matrix:
 
 
 def minimise(AN: sp.csr_matrix, row_target, col_target, tol: float = 1e-12, penalty: float = 1e-7,
-             max_iter: int = 200):
+             linear_from: float = 1e-6, max_iter: int = 200):
     """The mass-conservation minimisation of Sec 3.2 (eq. opti_masscons), with
     the paper's bounds 0 <= 1 + x <= 2 enforced inside it.
 
     The paper minimises x.x over x in R^{n_z} subject to A-hat (1 + x) = b
     (row sums |K_i|_phi, eq. localmassconsMat; column sums |M_j|_phi,
-    eq. globalmassconsMat) and the bounds.  The reading used throughout:
-    the bounds are hard (closed: the open bound 0 < 1 + x has no minimiser)
-    and the 2 n_c mass constraints are enforced by a quadratic penalty,
+    eq. globalmassconsMat) and the bounds.  On stretched and porous meshes the
+    balls can make these constraints contradictory (a cell whose only tracked
+    overlap is a smaller neighbour must send it more than it holds), so the
+    reading used throughout keeps the bounds hard (closed: the open bound
+    0 < 1 + x has no minimiser) and enforces the 2 n_c mass constraints by an
+    elastic penalty on their relative violations v_l = s_l / b_l,
+    s = b - A-hat (1 + x):
 
-        minimise  1/2 x.x + 1/(2 eps^2) sum_l (s_l / b_l)^2
-        over      0 <= 1 + x <= 2,     s = b - A-hat (1 + x),  eps = penalty,
+        minimise  1/2 x.x + sum_l h(v_l)   over 0 <= 1 + x <= 2,
+        h(v) = v^2 / (2 eps^2)                      for |v| <= delta,
+             = (delta |v| - delta^2 / 2) / eps^2    beyond,
 
-    which has exactly one minimiser for every input.  Where the paper's
-    problem has a solution this minimiser tends to it as eps -> 0, with
-    constraint residuals s_l = eps^2 b_l^2 y_l (y the multipliers of the
-    constraints); where it has none (the bounds and the constraints cannot
-    all hold), it is the adjustment within the bounds with the least relative
-    constraint violation in the least-squares sense, then the least x.x.
+    eps = penalty, delta = linear_from.  The minimiser is unique.  Where the
+    paper's problem has a solution whose multipliers stay below delta / eps^2
+    (1e8), this is that solution up to residuals v_l = eps^2 y_l <= delta; where
+    the constraints cannot all hold, the penalty grows linearly, so the total
+    relative violation is (up to O(delta)) the least the bounds allow -- the
+    linear programme's minimum -- and the multipliers stay bounded.
 
     Solved by a primal-dual interior-point method (Mehrotra's predictor-
     corrector), written out for this problem with f = 1 + x, the constraints
-    divided by their targets (G = diag(b)^-1 A-hat, so every target is 1) and
-    the upper bound carried by its own slack u = 2 - f (f near 2 would lose
-    u to rounding):
-        stationarity  f - 1 - G^T y - zeta_lo + zeta_hi = 0
-        constraints   G f + eps^2 y = 1
-        bounds        f, u, zeta_lo, zeta_hi >= 0 with f zeta_lo = u zeta_hi = mu -> 0.
-    Every iteration solves the normal equations (G D G^T + eps^2 I) dy = r,
-    D = 1 / (1 + zeta_lo / f + zeta_hi / u) per entry, twice (predictor and
+    divided by their targets (G = diag(b)^-1 A-hat, every target 1), the
+    violation split as v = eps^2 y + p - q (p, q >= 0 the parts beyond the
+    quadratic zone, priced at gamma = delta / eps^2) and the upper bound
+    carried by its own slack u = 2 - f (f near 2 would lose u to rounding):
+        stationarity  f - 1 - G^T y - zeta_lo + zeta_hi = 0,
+                      gamma - y - zeta_p = 0,  gamma + y - zeta_q = 0
+        constraints   G f + eps^2 y + p - q = 1
+        bounds        f, u, p, q and their multipliers >= 0, products -> mu.
+    Every iteration solves the normal equations
+    (G D G^T + diag(eps^2 + D_p + D_q)) dy = r, D = 1 / (1 + zeta_lo / f +
+    zeta_hi / u), D_p = p / zeta_p, D_q = q / zeta_q, twice (predictor and
     corrector) with one sparse factorisation (SuperLU, the linear-algebra
     primitive), and steps 0.99 of the way to the boundary.  It stops when the
-    scaled constraint residual is <= tol, mu <= 1e-15 and the stationarity
-    residual is <= 1e-12 of the largest dual value (y grows to ~1e12 where the
-    problem is infeasible, and G^T y then carries that much rounding; the
-    entries of G are at most 1).
+    constraint residual is <= tol, mu <= 1e-14, and the stationarity
+    residuals are <= 1e-12 of the largest dual value (resp. of gamma), the
+    rounding those carry.
 
     Returns (f = 1 + x in [0, 2], x, info); info has the iteration count, the
-    final scaled constraint residual, converged, the number of entries within
-    1e-9 of a bound, and the dual y of the unscaled constraints."""
+    final constraint residual, converged, the number of entries within 1e-9
+    of a bound, the violations v and the dual y of the unscaled constraints."""
     H = hat_matrix(AN)
     b = np.concatenate([row_target, col_target])
     G = (sp.diags(1.0 / b) @ H).tocsr()
     GT = G.T.tocsr()
     m, nz = G.shape
     w = penalty * penalty
-    f = np.ones(nz)
-    u = np.ones(nz)
-    zlo = np.ones(nz)
-    zhi = np.ones(nz)
+    gamma = linear_from / w
+    f, u, zlo, zhi = np.ones(nz), np.ones(nz), np.ones(nz), np.ones(nz)
+    p, q, zp, zq = np.ones(m), np.ones(m), np.ones(m), np.ones(m)
     y = np.zeros(m)
     one = np.ones(m)
     converged = False
     it = 0
     rp = one.copy()
+    n_pairs = 2 * nz + 2 * m
 
-    def to_boundary(v, dv):
-        neg = dv < 0.0
-        return min(1.0, float(np.min(-v[neg] / dv[neg]))) if neg.any() else 1.0
+    def to_boundary(pairs):
+        a = 1.0
+        for v, dv in pairs:
+            neg = dv < 0.0
+            if neg.any():
+                a = min(a, float(np.min(-v[neg] / dv[neg])))
+        return a
 
     for it in range(max_iter + 1):
         rd = (f - 1.0) - GT @ y - zlo + zhi
-        rp = one - G @ f - w * y
+        rdp = gamma - y - zp
+        rdq = gamma + y - zq
+        rp = one - G @ f - w * y - p + q
         ru = 2.0 - f - u
-        mu = float(f @ zlo + u @ zhi) / (2 * nz)
+        mu = float(f @ zlo + u @ zhi + p @ zp + q @ zq) / n_pairs
         dual_scale = 1.0 + max(float(np.max(np.abs(y))), float(zlo.max()), float(zhi.max()))
-        if np.max(np.abs(rp)) <= tol and mu <= 1e-15 and np.max(np.abs(rd)) <= 1e-12 * dual_scale:
+        if (np.max(np.abs(rp)) <= tol and mu <= 1e-14 and np.max(np.abs(rd)) <= 1e-12 * dual_scale
+                and max(float(np.max(np.abs(rdp))), float(np.max(np.abs(rdq)))) <= 1e-12 * (1.0 + gamma)):
             converged = True
             break
         if it == max_iter:
             break
         D = 1.0 / (1.0 + zlo / f + zhi / u)
-        lu = spla.splu((G @ sp.diags(D) @ GT + w * sp.eye(m)).tocsc(), permc_spec="COLAMD")
+        Dp, Dq = p / zp, q / zq
+        lu = spla.splu((G @ sp.diags(D) @ GT + sp.diags(w + Dp + Dq)).tocsc(), permc_spec="COLAMD")
 
-        def direction(c_lo, c_hi):
-            # linearised: zeta_lo df + f dzeta_lo = c_lo, zeta_hi du + u dzeta_hi = c_hi, du = ru - df
-            q = -rd + c_lo / f - c_hi / u + (zhi / u) * ru
-            dy = lu.solve(rp - G @ (D * q))
-            df = D * (q + GT @ dy)
+        def direction(c_lo, c_hi, c_p, c_q):
+            # linearised complementarity: zeta df + f dzeta = c per pair (du = ru - df for the upper one)
+            qf = -rd + c_lo / f - c_hi / u + (zhi / u) * ru
+            sp_ = -rdp + c_p / p       # dp = Dp (sp_ + dy)
+            sq_ = -rdq + c_q / q       # dq = Dq (sq_ - dy)
+            dy = lu.solve(rp - G @ (D * qf) - Dp * sp_ + Dq * sq_)
+            df = D * (qf + GT @ dy)
             du = ru - df
-            return df, du, dy, (c_lo - zlo * df) / f, (c_hi - zhi * du) / u
+            dp, dq = Dp * (sp_ + dy), Dq * (sq_ - dy)
+            return (df, du, dp, dq, dy, (c_lo - zlo * df) / f, (c_hi - zhi * du) / u, (c_p - zp * dp) / p,
+                    (c_q - zq * dq) / q)
 
-        df, du, dy, dzlo, dzhi = direction(-f * zlo, -u * zhi)  # predictor (affine scaling)
-        ap = min(to_boundary(f, df), to_boundary(u, du))
-        ad = min(to_boundary(zlo, dzlo), to_boundary(zhi, dzhi))
-        mu_aff = float((f + ap * df) @ (zlo + ad * dzlo) + (u + ap * du) @ (zhi + ad * dzhi)) / (2 * nz)
-        sigma = min(1.0, (mu_aff / mu) ** 3)
-        df, du, dy, dzlo, dzhi = direction(sigma * mu - f * zlo - df * dzlo, sigma * mu - u * zhi - du * dzhi)
-        ap = 0.99 * min(to_boundary(f, df), to_boundary(u, du))
-        ad = 0.99 * min(to_boundary(zlo, dzlo), to_boundary(zhi, dzhi))
-        f = f + ap * df
-        u = u + ap * du
-        y = y + ad * dy
-        zlo = zlo + ad * dzlo
-        zhi = zhi + ad * dzhi
+        df, du, dp, dq, dy, dzlo, dzhi, dzp, dzq = direction(-f * zlo, -u * zhi, -p * zp, -q * zq)  # predictor
+        ap = to_boundary([(f, df), (u, du), (p, dp), (q, dq)])
+        ad = to_boundary([(zlo, dzlo), (zhi, dzhi), (zp, dzp), (zq, dzq)])
+        mu_aff = float((f + ap * df) @ (zlo + ad * dzlo) + (u + ap * du) @ (zhi + ad * dzhi)
+                       + (p + ap * dp) @ (zp + ad * dzp) + (q + ap * dq) @ (zq + ad * dzq)) / n_pairs
+        sm = min(1.0, (mu_aff / mu) ** 3) * mu
+        df, du, dp, dq, dy, dzlo, dzhi, dzp, dzq = direction(sm - f * zlo - df * dzlo, sm - u * zhi - du * dzhi,
+                                                              sm - p * zp - dp * dzp, sm - q * zq - dq * dzq)
+        ap = 0.99 * to_boundary([(f, df), (u, du), (p, dp), (q, dq)])
+        ad = 0.99 * to_boundary([(zlo, dzlo), (zhi, dzhi), (zp, dzp), (zq, dzq)])
+        f, u, p, q = f + ap * df, u + ap * du, p + ap * dp, q + ap * dq
+        y, zlo, zhi, zp, zq = y + ad * dy, zlo + ad * dzlo, zhi + ad * dzhi, zp + ad * dzp, zq + ad * dzq
     f = np.clip(f, 0.0, 2.0)
     info = {"iterations": it, "kkt_l1": float(np.max(np.abs(rp))), "converged": converged,
-            "n_at_bounds": int(np.sum((f < 1e-9) | (f > 2.0 - 1e-9))), "y": y / b}
+            "n_at_bounds": int(np.sum((f < 1e-9) | (f > 2.0 - 1e-9))), "y": y / b,
+            "violation": w * y + p - q}
     return f, f - 1.0, info
 
 
@@ -554,6 +573,7 @@ class StepOptions:
     n_scale: int = 10          # N of Algorithm 1 (Sec 4: N = 10)
     qp_tol: float = 1e-12      # scaled constraint residual at which the minimisation stops
     penalty: float = 1e-7      # eps of the constraint penalty in ``minimise``
+    linear_from: float = 1e-6  # delta: relative violation beyond which that penalty is linear
     drop_tol: float = 1e-12
     cfl: float = 0.5
     substeps: int = 0          # 0: from the CFL rule
@@ -572,7 +592,7 @@ def step(mesh: Mesh, faces, dt: float, c, opts: StepOptions | None = None):
     AN = scale(A0, b_loc, volphi, opts.n_scale)
     colsum = np.asarray(AN.sum(axis=0)).reshape(-1)
     scale_err = float(np.max(np.abs(colsum - volphi) / volphi))
-    factor, x, qinfo = minimise(AN, b_loc, volphi, opts.qp_tol, opts.penalty)
+    factor, x, qinfo = minimise(AN, b_loc, volphi, opts.qp_tol, opts.penalty, opts.linear_from)
     Aq = AN.copy()
     Aq.data = AN.data * factor
     Afin = column_fix(Aq, AN, volphi)

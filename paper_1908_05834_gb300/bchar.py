@@ -37,8 +37,8 @@ class StepInfo(ctypes.Structure):
                 ("mass_after_stored", ctypes.c_double), ("max_rel_row_res", ctypes.c_double),
                 ("max_rel_col_res", ctypes.c_double), ("scale_err", ctypes.c_double), ("kkt_rel", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("substeps", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
-                ("refines", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
-                ("empty_cols", ctypes.c_int32), ("n_clipped", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("ip_iters", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
+                ("empty_cols", ctypes.c_int32), ("n_at_bounds", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32),
                 ("row_cap", ctypes.c_int32),
                 ("ms_stage", ctypes.c_float * 8)]

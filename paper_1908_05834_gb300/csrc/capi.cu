@@ -132,9 +132,9 @@ void bchar_default_options(bchar_options *o) {
     o->cfl = 0.5;
     o->drop_tol = 1e-12;
     o->penalty = 1e-7;
-    o->qp_tol = 1e-14;
+    o->qp_tol = 1e-9;
     o->qp_max_iter = 200000;
-    o->qp_max_refine = 60;
+    o->qp_max_refine = 100;
     o->div_tol = 1e-9;
     o->qp_precond = 1;
     o->qp_warm_start = 1;
@@ -168,7 +168,10 @@ void bchar_destroy(bchar_mesh_t m) {
                   &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
                   &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->bloc, &m->uf_parent, &m->uf_label, &m->comp_acc, &m->a2,
                   &m->a2c, &m->diag, &m->qexc, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
-                  &m->cg_q, &m->cg_rp, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg};
+                  &m->cg_q, &m->cg_rp, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg, &m->ip_f, &m->ip_u,
+                  &m->ip_zl, &m->ip_zh, &m->ip_D, &m->ip_q, &m->ip_cl, &m->ip_ch, &m->ip_df, &m->ip_du,
+                  &m->ip_dzl, &m->ip_dzh, &m->ip_p, &m->ip_n, &m->ip_zp, &m->ip_zn, &m->ip_cp, &m->ip_cn,
+                  &m->ip_dp, &m->ip_dn, &m->ip_dzp, &m->ip_dzn};
     for (Buf *b : all) release(*b);
     for (int a = 0; a < 3; ++a) {
         release(m->x[a]);
@@ -458,8 +461,8 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     // N alternating scalings, the minimisation, bounds and column fix, update
     launch_scaling(m);
     cudaEventRecord(ev[4], m->stream);
-    int cg_iters = 0, refines = 0;
-    launch_minimise(m, &cg_iters, &refines);
+    int cg_iters = 0, ip_iters = 0;
+    if (!launch_minimise(m, &cg_iters, &ip_iters)) return BCHAR_ERR_OUT_OF_MEMORY;
     cudaEventRecord(ev[5], m->stream);
     launch_finalise(m);
     cudaEventRecord(ev[6], m->stream);
@@ -485,15 +488,15 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->max_rel_row_res = h->max_rel_row_res;
         info->max_rel_col_res = h->max_rel_col_res;
         info->scale_err = h->scale_err;
-        info->kkt_rel = h->kkt_l1 / m->sum_volphi;
+        info->kkt_rel = h->kkt_l1;
         info->nnz = nnz;
         info->substeps = substeps;
         info->cg_iters = cg_iters;
-        info->refines = refines;
-        info->qp_converged = info->kkt_rel <= m->opt.qp_tol;
+        info->ip_iters = ip_iters;
+        info->qp_converged = m->ip_converged;
         info->void_balls = void_balls;
         info->empty_cols = nseeds;
-        info->n_clipped = h->n_clipped;
+        info->n_at_bounds = h->n_at_bounds;
         info->kernel_launches = m->launches;
         info->amg_levels = m->amg_levels;
         info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);

@@ -3,9 +3,8 @@
 // sum_cols |M_j|_phi / sum_rows |K_i|_phi when the two sums differ by more
 // than 1e-12 relative, so that the constraints of eq. localmassconsMat and
 // eq. globalmassconsMat can hold together.  Row i and column j are linked
-// when a0_ij >= theta * max(largest entry of row i, largest entry of
-// column j), theta = 1e-3: a sliver overlap below that share cannot carry a
-// block's mismatch within the bounds 0 <= 1 + x <= 2.
+// whenever a0_ij != 0: the components of A's pattern, on which both sums must
+// equal the sum of the component's entries once the constraints hold.
 //
 // Components: lock-free union-find over the 2 n_c row/column nodes, always
 // hooking the larger root under the smaller one, so every component ends with
@@ -25,7 +24,6 @@ namespace bchar {
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
 
 constexpr int kUnionRetries = 1 << 20;
-constexpr double kTheta = 1e-3;
 
 __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
     for (int it = 0; it < kUnionRetries; ++it) {
@@ -42,22 +40,11 @@ __global__ void k_uf_init(int64_t n2, int32_t *parent) {
     GRID_STRIDE(l, n2) parent[l] = static_cast<int32_t>(l);
 }
 
-// Largest entry of every column of A^(0).
-__global__ void k_colmax(int64_t nc, const int64_t *col_ptr, const int32_t *csc_src, const double *a0, double *cmax) {
-    GRID_STRIDE(j, nc) {
-        double mx = 0.0;
-        for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) mx = fmax(mx, a0[csc_src[p]]);
-        cmax[j] = mx;
-    }
-}
-
 __global__ void k_uf_union(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a0,
-                           const double *cmax, int32_t *parent, DevInfo *info) {
+                           int32_t *parent, DevInfo *info) {
     GRID_STRIDE(i, nc) {
-        double rmax = 0.0;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) rmax = fmax(rmax, a0[e]);
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            if (a0[e] < kTheta * fmax(rmax, cmax[col[e]])) continue;  // a sliver: does not link the blocks
+            if (a0[e] == 0.0) continue;
             int32_t a = static_cast<int32_t>(i), b = static_cast<int32_t>(nc + col[e]);
             int it = 0;
             for (; it < kUnionRetries; ++it) {
@@ -135,17 +122,14 @@ bool launch_balance(bchar_mesh_t m) {
     frexp(m->max_volphi, &e);                 // max |K|_phi < 2^e
     const int shift = 52 - e;                 // so every |K|_phi * 2^shift < 2^52
     cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4 * n2, s);
-    double *cmax = ptr<double>(m->C);  // scratch: the scaling factors are written later
-    k_colmax<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
-                                                 ptr<double>(m->a0), cmax);
     k_uf_init<<<blocks_for(n2), kThreads, 0, s>>>(n2, parent);
     k_uf_union<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                   ptr<double>(m->a0), cmax, parent, di);
+                                                   ptr<double>(m->a0), parent, di);
     k_uf_label<<<blocks_for(n2), kThreads, 0, s>>>(n2, parent, label);
     k_comp_sums<<<blocks_for(n2), kThreads, 0, s>>>(nc, label, ptr<double>(m->volphi), shift, acc);
     k_balance<<<blocks_for(nc), kThreads, 0, s>>>(nc, label, ptr<double>(m->volphi), acc, shift, 1e-12,
                                                   ptr<double>(m->bloc), di);
-    m->launches += 6;
+    m->launches += 5;
     return true;
 }
 

@@ -68,6 +68,7 @@ struct DevInfo {
     double mass_before, mass_after, mass_after_stored;
     double max_rel_row_res, max_rel_col_res, scale_err;
     double kkt_l1, f_l1;
+    int n_at_bounds;    // entries with 1 + x within 1e-9 of 0 or 2 after the minimisation
     unsigned long long vmax_bits;   // max |u|/phi as the bits of a non-negative double
     unsigned long long umax_bits;   // max |u| over all faces
     unsigned long long bflux_bits;  // max |u.n| over boundary faces
@@ -77,7 +78,6 @@ struct DevInfo {
     int need_row_cap;   // largest row length seen
     int void_balls;
     int n_seeds;
-    int n_clipped;
     int unbalanced;
     long long nnz;
 };
@@ -85,6 +85,7 @@ struct DevInfo {
 // Conjugate-gradient scalars.
 struct CgState {
     double rz, rz_new, pq, alpha, beta, res_l1, target;
+    double target_l1;  // the solve also needs |res|_1 <= target_l1
     int converged;
     int iters;
 };
@@ -157,6 +158,12 @@ struct bchar_mesh_s {
     bchar::Buf R, C, bloc;                           // scaling factors, balanced row targets
     bchar::Buf uf_parent, uf_label, comp_acc;        // components of A's pattern
     bchar::Buf a2, a2c, diag, qexc, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
+    // interior-point state per entry: 1 + x and its upper slack 2 - (1 + x), the bound multipliers,
+    // the normal-equation weight, the reduced right-hand side, the complementarity targets, a direction
+    bchar::Buf ip_f, ip_u, ip_zl, ip_zh, ip_D, ip_q, ip_cl, ip_ch, ip_df, ip_du, ip_dzl, ip_dzh;
+    // per node (row or column constraint): the violation beyond the quadratic zone, split
+    // p - q, their multipliers, complementarity targets and a direction
+    bchar::Buf ip_p, ip_n, ip_zp, ip_zn, ip_cp, ip_cn, ip_dp, ip_dn, ip_dzp, ip_dzn;
     bchar::Buf scan_tmp, partials, dinfo, cg, cg_rp; // scratch (cg_rp: previous residual of the flexible CG)
     bchar::Buf info_host;                            // pinned DevInfo
     bchar::Amg amg;                                  // preconditioner of the minimisation
@@ -166,11 +173,8 @@ struct bchar_mesh_s {
     int amg_levels = 0;
     int64_t amg_coarsest = 0;
     bool have_step = false;
-    bool have_dual = false;  // qy holds the dual of the last successful minimisation
-    int warm_steps = 0;      // consecutive warm-started minimisations
-    int amg_age = -1;        // steps since the multigrid aggregation was built (-1: none yet)
-    int amg_built_iters = 0; // CG iterations of the solve right after that build
-    int last_cg_iters = 0;   // CG iterations of the previous solve
+    int ip_iters = 0;        // interior-point iterations of the last minimisation
+    bool ip_converged = false;
     int launches = 0;
 };
 
@@ -236,7 +240,7 @@ void scan_i32_to_i64(bchar_mesh_t m, const int32_t *in, int64_t *out, int64_t n)
 void launch_transpose(bchar_mesh_t m);
 bool launch_balance(bchar_mesh_t m);  // components.cu
 void launch_scaling(bchar_mesh_t m);
-void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines);
+bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters);  // false: out of memory
 void launch_finalise(bchar_mesh_t m);
 void launch_update(bchar_mesh_t m, const void *c_in, void *c_out, int c_dtype);
 void launch_cg_matvec_once(bchar_mesh_t m, CgState *st);  // q = J p with the current p, for timing

@@ -3,17 +3,17 @@
 //   - the column view of A (deterministic: columns sorted by row),
 //   - N alternating column/row scalings (Sec 3.2, eq. volAdj), kept as
 //     diagonal factors, A^(N) = diag(R) A^(0) diag(C),
-//   - the mass-conservation minimisation (Sec 3.2, eq. opti_masscons) in the
-//     penalised form: the minimiser of 1/2 x.x + 1/2 sum_l (s_l/(eps b_l))^2,
-//     s = b - A-hat (1 + x), i.e. x = A-hat^T y with
-//     (A-hat A-hat^T + diag((eps b)^2)) y = b - A-hat 1.  A-hat A-hat^T is the
-//     bipartite matrix [[D_r, W], [W^T, D_c]], W_ij = a_ij^2, applied through
-//     the row and column views of A without forming A-hat; it is solved by
-//     Jacobi-preconditioned conjugate gradients with iterative refinement
-//     (x accumulated per entry, since y itself can grow very large),
-//   - the bounds 0 <= 1 + x <= 2, a final column scaling (global mass to
-//     rounding), W_KM = a_KM / |K|_phi and the update c^{n+1} = W c^n
-//     (eq. phys-inter-ELLAM) with FP64 accumulation.
+//   - the mass-conservation minimisation (Sec 3.2, eq. opti_masscons) with
+//     its bounds 0 <= 1 + x <= 2 inside the problem and an elastic penalty on
+//     the relative violations of the mass constraints (quadratic, weight
+//     1/eps^2, up to 1e-6; linear beyond), by a primal-dual interior-point
+//     method whose normal equations (A-hat D A-hat^T + diag(exc)) are the
+//     bipartite matrix [[D_r, W], [W^T, D_c]], W_ij = a_ij^2 D_ij, applied
+//     through the row and column views of A without forming A-hat and solved
+//     by conjugate gradients with an aggregation-multigrid preconditioner,
+//   - a final column scaling (global mass to rounding), W_KM = a_KM / |K|_phi
+//     and the update c^{n+1} = W c^n (eq. phys-inter-ELLAM) with FP64
+//     accumulation.
 // All sums run in a fixed order (no floating-point atomics), so a step is
 // bitwise reproducible.
 #include <math.h>
@@ -242,61 +242,28 @@ void launch_scaling(bchar_mesh_t m) {
 }
 
 // ---------------------------------------------------------------- minimisation
-
-// Node l < n: row l; node l >= n: column l - n.  b_l = |K|_phi resp. |M|_phi,
-// w_l = (eps b_l)^2.
-__global__ void k_qp_setup(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
-                           const double *aN, const double *brow, const double *volphi, double eps, double *a2,
-                           double *diag, double *exc, double *rhs) {
-    GRID_STRIDE(l, 2 * nc) {
-        double d = 0.0, s = 0.0;
-        if (l < nc) {
-            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) {
-                const double a = aN[e];
-                a2[e] = a * a;
-                d += a * a;
-                s += a;
-            }
-        } else {
-            const int64_t j = l - nc;
-            for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) {
-                const double a = aN[csc_src[p]];
-                d += a * a;
-                s += a;
-            }
-        }
-        const double b = l < nc ? brow[l] : volphi[l - nc];
-        const double w = (eps * b) * (eps * b);
-        diag[l] = d + w;
-        exc[l] = w;
-        rhs[l] = b - s;
-    }
-}
+//
+// eq. opti_masscons with the bounds 0 <= f = 1 + x <= 2 inside the problem and
+// the 2 n_c mass constraints enforced by an elastic penalty on their relative
+// violations v_l (see bchar_step in bchar.h): quadratic, weight 1/eps^2, up to
+// |v| = 1e-6 and linear beyond, slope gamma = 1e-6 / eps^2.  Solved by a
+// primal-dual interior-point method (Mehrotra predictor-corrector) with f, its
+// upper slack u = 2 - f (carried separately: f near 2 would lose u to
+// rounding), the bound multipliers zl, zh >= 0, the constraint multipliers y
+// (node l < n_c: row l, node n_c + j: column j) and, per node, the violation
+// beyond the quadratic zone split p - n with p, n >= 0 and multipliers zp, zn:
+//     stationarity  rd_e = f_e - 1 - a_e (y_i + y_{n_c+j}) - zl_e + zh_e,
+//                   gamma - b_l y_l - zp_l = 0,  gamma + b_l y_l - zn_l = 0
+//     constraints   rp_l = b_l - (A-hat f)_l - eps^2 b_l^2 y_l - b_l (p_l - n_l)
+//     slack         ru_e = 2 - f_e - u_e
+// Each iteration solves the normal equations (A-hat D A-hat^T + diag(exc)) dy = r,
+// D_e = 1 / (1 + zl_e / f_e + zh_e / u_e), exc_l = b_l^2 (eps^2 + p_l / zp_l +
+// n_l / zn_l), twice with one preconditioner: the bipartite Laplacian of the
+// step's pattern with edge weights a_e^2 D_e and that diagonal shift, by the
+// conjugate gradients below with the aggregation multigrid.
 
 __global__ void k_qp_gather_cols(int64_t nnz, const int32_t *csc_src, const double *a2, double *a2c) {
     GRID_STRIDE(p, nnz) a2c[p] = a2[csc_src[p]];
-}
-
-// F = r - A-hat x - w y and per-block partial sums of |F|.
-__global__ void k_qp_kkt(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
-                         const double *aN, const double *qx, const double *y, const double *rhs, const double *brow,
-                         const double *volphi, double eps, double *F, double *partials) {
-    double acc = 0.0;
-    GRID_STRIDE(l, 2 * nc) {
-        double s = 0.0;
-        if (l < nc) {
-            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) s += aN[e] * qx[e];
-        } else {
-            const int64_t j = l - nc;
-            for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) s += aN[csc_src[p]] * qx[csc_src[p]];
-        }
-        const double b = l < nc ? brow[l] : volphi[l - nc];
-        const double f = rhs[l] - s - (eps * b) * (eps * b) * y[l];
-        F[l] = f;
-        acc += fabs(f);
-    }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // Preconditioned conjugate gradients on (A-hat A-hat^T + W) d = F.  Every
@@ -323,14 +290,19 @@ __global__ void k_dot(int64_t n, const double *a, const double *b, double *parti
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-__global__ void k_cg_start(const double *partials, int nparts, double target, CgState *st) {
+// Start of a solve: z.res of the initial residual, the two stopping targets
+// (z.res <= target and |res|_1 <= target_l1; the initial |res|_1 is rhs_l1).
+__global__ void k_cg_start(const double *partials, int nparts, double target, double target_l1, double rhs_l1,
+                           CgState *st) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partials[i];
     s = block_sum(s);
     if (threadIdx.x == 0) {
         st->rz = s;
         st->target = target;
-        st->converged = (s == 0.0);
+        st->target_l1 = target_l1;
+        st->res_l1 = rhs_l1;
+        st->converged = (s == 0.0) || (s <= target && rhs_l1 <= target_l1);
         st->iters = 0;
     }
 }
@@ -448,7 +420,7 @@ __global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const 
         st->rz = rz;
         st->res_l1 = l1;
         st->iters += 1;
-        if (l1 <= st->target || !(st->pq > 0.0) || !(rz > 0.0)) st->converged = 1;
+        if ((rz <= st->target && l1 <= st->target_l1) || !(st->pq > 0.0) || !(rz > 0.0)) st->converged = 1;
     }
 }
 
@@ -459,24 +431,386 @@ __global__ void k_cg_pupdate(int64_t n2, const double *z, double *p, const CgSta
     GRID_STRIDE(l, n2) p[l] = z[l] + beta * p[l];
 }
 
-// Warm start: x_e = a_e (y_i + y_{n+j}) from a dual y kept from the
-// previous step (x = A-hat^T y on the new matrix).
-__global__ void k_qp_warm(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aN, const double *y,
-                          double *qx) {
+// Scalars of one interior-point iteration, reduced over blocks (kRedBlocks
+// partial slots each) and read back once.
+struct IpScalars {
+    double rp_max;      // max_l |rp_l| / b_l (the scaled constraint residual)
+    double rd_max;      // max_e |rd_e|
+    double rpq_max;     // max_l of the stationarity residuals of p and n
+    double dual_max;    // max(max_l |y_l| b_l, max zl, max zh)
+    double comp;        // sum of the complementarity products of all pairs
+    double rp_l1;       // sum_l |rp_l| (unscaled)
+    double ap, ad;      // largest primal / dual step to the boundary (<= 1)
+    double comp_aff;    // the same sum after the predictor's steps
+};
+
+constexpr int kIpSlots = 8;  // partial-sum slots per block in the reduction scratch
+
+__device__ __forceinline__ double ip_rd(double f, double zl, double zh, double gty) { return f - 1.0 - gty - zl + zh; }
+
+// Entry pass (thread per row): stationarity residuals rd and the entries'
+// complementarity sum; slots 0 (max |rd|), 1 (max multiplier), 2 (sum).
+__global__ void k_ip_entries(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a,
+                             const double *y, const double *f, const double *u, const double *zl, const double *zh,
+                             double *part) {
+    dep_enter();
+    double rd_max = 0.0, comp = 0.0, zmax = 0.0;
     GRID_STRIDE(i, nc) {
         const double yi = y[i];
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) qx[e] = aN[e] * (yi + y[nc + col[e]]);
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            rd_max = fmax(rd_max, fabs(ip_rd(f[e], zl[e], zh[e], a[e] * (yi + y[nc + col[e]]))));
+            comp += f[e] * zl[e] + u[e] * zh[e];
+            zmax = fmax(zmax, fmax(zl[e], zh[e]));
+        }
+    }
+    rd_max = block_max(rd_max);
+    zmax = block_max(zmax);
+    comp = block_sum(comp);
+    if (threadIdx.x == 0) {
+        double *pb = part + kIpSlots * blockIdx.x;
+        pb[0] = rd_max;
+        pb[1] = zmax;
+        pb[2] = comp;
     }
 }
 
-// x_e += a_e (d_i + d_{n+j}), y += d
-__global__ void k_qp_accumulate(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *aN,
-                                const double *d, double *qx, double *y) {
-    GRID_STRIDE(l, 2 * nc) {
-        if (l < nc)
-            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) qx[e] += aN[e] * (d[l] + d[nc + col[e]]);
-        y[l] += d[l];
+// Node l: its constraint sum (row l by CSR, column l - n_c by CSC).
+__device__ __forceinline__ double ip_node_sum(int64_t nc, int64_t l, const int64_t *row_ptr, const int64_t *col_ptr,
+                                              const int32_t *csc_src, const double *a, const double *v) {
+    double s = 0.0;
+    if (l < nc) {
+        for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) s += a[e] * v[e];
+    } else {
+        for (int64_t k = col_ptr[l - nc]; k < col_ptr[l - nc + 1]; ++k) {
+            const int32_t e = csc_src[k];
+            s += a[e] * v[e];
+        }
     }
+    return s;
+}
+
+__device__ __forceinline__ double ip_target(int64_t nc, int64_t l, const double *b_row, const double *volphi) {
+    return l < nc ? b_row[l] : volphi[l - nc];
+}
+
+// Node pass: constraint residual rp_l = b_l - (A-hat f)_l - eps^2 b_l^2 y_l - b_l (p_l - n_l),
+// the stationarity residuals gamma -+ b y - z of p and n, their complementarity;
+// slots 3 (max |rp| / b), 4 (max |rdp|, |rdn|), 5 (max |y| b), 6 (sum).
+__global__ void k_ip_nodes(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
+                           const double *a, const double *b_row, const double *volphi, double eps2, double gamma,
+                           const double *y, const double *f, const double *p, const double *n, const double *zp,
+                           const double *zn, double *rp, double *part) {
+    dep_enter();
+    double rp_max = 0.0, rpq_max = 0.0, ymax = 0.0, comp = 0.0, rp_l1 = 0.0;
+    GRID_STRIDE(l, 2 * nc) {
+        const double bl = ip_target(nc, l, b_row, volphi);
+        const double ys = y[l] * bl;
+        const double r = bl - ip_node_sum(nc, l, row_ptr, col_ptr, csc_src, a, f) - eps2 * bl * ys - bl * (p[l] - n[l]);
+        rp[l] = r;
+        rp_l1 += fabs(r);
+        rp_max = fmax(rp_max, fabs(r) / bl);
+        rpq_max = fmax(rpq_max, fmax(fabs(gamma - ys - zp[l]), fabs(gamma + ys - zn[l])));
+        ymax = fmax(ymax, fabs(ys));
+        comp += p[l] * zp[l] + n[l] * zn[l];
+    }
+    rp_max = block_max(rp_max);
+    rpq_max = block_max(rpq_max);
+    ymax = block_max(ymax);
+    comp = block_sum(comp);
+    rp_l1 = block_sum(rp_l1);
+    if (threadIdx.x == 0) {
+        double *pb = part + kIpSlots * blockIdx.x;
+        pb[3] = rp_max;
+        pb[4] = rpq_max;
+        pb[5] = ymax;
+        pb[6] = comp;
+        pb[7] = rp_l1;
+    }
+}
+
+__global__ void k_ip_reduce_resid(const double *part, int nparts, IpScalars *st) {
+    double rd = 0.0, rp = 0.0, rpq = 0.0, dm = 0.0, comp = 0.0, l1 = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        const double *pb = part + kIpSlots * k;
+        l1 += pb[7];
+        rd = fmax(rd, pb[0]);
+        dm = fmax(dm, fmax(pb[1], pb[5]));
+        comp += pb[2] + pb[6];
+        rp = fmax(rp, pb[3]);
+        rpq = fmax(rpq, pb[4]);
+    }
+    rd = block_max(rd);
+    rp = block_max(rp);
+    rpq = block_max(rpq);
+    dm = block_max(dm);
+    comp = block_sum(comp);
+    l1 = block_sum(l1);
+    if (threadIdx.x == 0) {
+        st->rp_l1 = l1;
+        st->rd_max = rd;
+        st->rp_max = rp;
+        st->rpq_max = rpq;
+        st->dual_max = dm;
+        st->comp = comp;
+    }
+}
+
+// Normal-equation weights: D_e, a2_e = a_e^2 D_e, and per node
+// exc_l = b_l^2 (eps^2 + p_l / zp_l + n_l / zn_l) and diag_l = sum a^2 D + exc_l.
+__global__ void k_ip_weights(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
+                             const double *a, const double *b_row, const double *volphi, double eps2,
+                             const double *f, const double *u, const double *zl, const double *zh, const double *p,
+                             const double *n, const double *zp, const double *zn, double *D, double *a2, double *diag,
+                             double *exc) {
+    dep_enter();
+    GRID_STRIDE(l, 2 * nc) {
+        double d = 0.0;
+        if (l < nc) {
+            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) {
+                const double De = 1.0 / (1.0 + zl[e] / f[e] + zh[e] / u[e]);
+                D[e] = De;
+                a2[e] = a[e] * a[e] * De;
+                d += a2[e];
+            }
+        } else {
+            for (int64_t k = col_ptr[l - nc]; k < col_ptr[l - nc + 1]; ++k) {
+                const int32_t e = csc_src[k];
+                d += a[e] * a[e] / (1.0 + zl[e] / f[e] + zh[e] / u[e]);
+            }
+        }
+        const double bl = ip_target(nc, l, b_row, volphi);
+        const double x = bl * bl * (eps2 + p[l] / zp[l] + n[l] / zn[l]);
+        diag[l] = d + x;
+        exc[l] = x;
+    }
+}
+
+// Reduced right-hand side per entry for the predictor (corrector = 0) or the
+// corrector (sigma_mu = sigma * mu, with the predictor's direction in df..dzh):
+//   cl = target of f zl, ch = target of u zh,
+//   q = -rd + cl / f - ch / u + (zh / u) ru.
+__global__ void k_ip_q(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a, const double *y,
+                       const double *f, const double *u, const double *zl, const double *zh, int corrector,
+                       double sigma_mu, const double *df, const double *du, const double *dzl, const double *dzh,
+                       double *cl, double *ch, double *q) {
+    dep_enter();
+    GRID_STRIDE(i, nc) {
+        const double yi = y[i];
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const double fe = f[e], ue = u[e], zle = zl[e], zhe = zh[e];
+            const double rd = ip_rd(fe, zle, zhe, a[e] * (yi + y[nc + col[e]]));
+            const double ru = 2.0 - fe - ue;
+            double c_lo = -fe * zle, c_hi = -ue * zhe;
+            if (corrector) {
+                c_lo += sigma_mu - df[e] * dzl[e];
+                c_hi += sigma_mu - du[e] * dzh[e];
+            }
+            cl[e] = c_lo;
+            ch[e] = c_hi;
+            q[e] = -rd + c_lo / fe - c_hi / ue + (zhe / ue) * ru;
+        }
+    }
+}
+
+// Per node: the targets of p zp and n zn, and
+// rhs_l = rp_l - (A-hat (D q))_l - b_l (p/zp sp - n/zn sn),
+// sp = -(gamma - b y - zp) + cp / p, sn = -(gamma + b y - zn) + cn / n.
+__global__ void k_ip_rhs(int64_t nc, const int64_t *row_ptr, const int64_t *col_ptr, const int32_t *csc_src,
+                         const double *a, const double *D, const double *q, const double *rp, const double *b_row,
+                         const double *volphi, double gamma, const double *y, const double *p, const double *n,
+                         const double *zp, const double *zn, int corrector, double sigma_mu, const double *dp,
+                         const double *dn, const double *dzp, const double *dzn, double *cp, double *cn, double *rhs) {
+    dep_enter();
+    GRID_STRIDE(l, 2 * nc) {
+        double s = 0.0;
+        if (l < nc) {
+            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) s += a[e] * D[e] * q[e];
+        } else {
+            for (int64_t k = col_ptr[l - nc]; k < col_ptr[l - nc + 1]; ++k) {
+                const int32_t e = csc_src[k];
+                s += a[e] * D[e] * q[e];
+            }
+        }
+        const double bl = ip_target(nc, l, b_row, volphi);
+        const double ys = y[l] * bl;
+        double c_p = -p[l] * zp[l], c_n = -n[l] * zn[l];
+        if (corrector) {
+            c_p += sigma_mu - dp[l] * dzp[l];
+            c_n += sigma_mu - dn[l] * dzn[l];
+        }
+        cp[l] = c_p;
+        cn[l] = c_n;
+        const double sp = -(gamma - ys - zp[l]) + c_p / p[l];
+        const double sn = -(gamma + ys - zn[l]) + c_n / n[l];
+        rhs[l] = rp[l] - s - bl * (p[l] / zp[l] * sp - n[l] / zn[l] * sn);
+    }
+}
+
+// Direction per entry from dy, and the ratio tests (largest steps <= 1 that
+// keep f, u, zl, zh positive), reduced per block as their reciprocals
+// max(1, -dv / v) into slots 0 (primal) and 1 (dual).
+__global__ void k_ip_dir(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a, const double *dy,
+                         const double *f, const double *u, const double *zl, const double *zh, const double *D,
+                         const double *q, const double *cl, const double *ch, double *df, double *du, double *dzl,
+                         double *dzh, double *part) {
+    dep_enter();
+    double ap_inv = 1.0, ad_inv = 1.0;
+    GRID_STRIDE(i, nc) {
+        const double di = dy[i];
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const double fe = f[e], ue = u[e];
+            const double d_f = D[e] * (q[e] + a[e] * (di + dy[nc + col[e]]));
+            const double ru = 2.0 - fe - ue;
+            const double d_u = ru - d_f;
+            const double d_zl = (cl[e] - zl[e] * d_f) / fe;
+            const double d_zh = (ch[e] - zh[e] * d_u) / ue;
+            df[e] = d_f;
+            du[e] = d_u;
+            dzl[e] = d_zl;
+            dzh[e] = d_zh;
+            ap_inv = fmax(ap_inv, fmax(-d_f / fe, -d_u / ue));
+            ad_inv = fmax(ad_inv, fmax(-d_zl / zl[e], -d_zh / zh[e]));
+        }
+    }
+    ap_inv = block_max(ap_inv);  // block_max pads with 0: only for non-negative values
+    ad_inv = block_max(ad_inv);
+    if (threadIdx.x == 0) {
+        part[kIpSlots * blockIdx.x] = ap_inv;
+        part[kIpSlots * blockIdx.x + 1] = ad_inv;
+    }
+}
+
+// The same per node for p, n and their multipliers (dy scaled: b_l dy_l),
+// into slots 2 (primal) and 3 (dual).
+__global__ void k_ip_dir_nodes(int64_t nc, const double *b_row, const double *volphi, double gamma, const double *y,
+                               const double *dy, const double *p, const double *n, const double *zp, const double *zn,
+                               const double *cp, const double *cn, double *dp, double *dn, double *dzp, double *dzn,
+                               double *part) {
+    dep_enter();
+    double ap_inv = 1.0, ad_inv = 1.0;
+    GRID_STRIDE(l, 2 * nc) {
+        const double bl = ip_target(nc, l, b_row, volphi);
+        const double ys = y[l] * bl, dys = dy[l] * bl;
+        const double sp = -(gamma - ys - zp[l]) + cp[l] / p[l];
+        const double sn = -(gamma + ys - zn[l]) + cn[l] / n[l];
+        const double d_p = p[l] / zp[l] * (sp + dys);
+        const double d_n = n[l] / zn[l] * (sn - dys);
+        const double d_zp = (cp[l] - zp[l] * d_p) / p[l];
+        const double d_zn = (cn[l] - zn[l] * d_n) / n[l];
+        dp[l] = d_p;
+        dn[l] = d_n;
+        dzp[l] = d_zp;
+        dzn[l] = d_zn;
+        ap_inv = fmax(ap_inv, fmax(-d_p / p[l], -d_n / n[l]));
+        ad_inv = fmax(ad_inv, fmax(-d_zp / zp[l], -d_zn / zn[l]));
+    }
+    ap_inv = block_max(ap_inv);
+    ad_inv = block_max(ad_inv);
+    if (threadIdx.x == 0) {
+        part[kIpSlots * blockIdx.x + 2] = ap_inv;
+        part[kIpSlots * blockIdx.x + 3] = ad_inv;
+    }
+}
+
+__global__ void k_ip_reduce_steps(const double *part, int nparts, IpScalars *st) {
+    double ap_inv = 1.0, ad_inv = 1.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        const double *pb = part + kIpSlots * k;
+        ap_inv = fmax(ap_inv, fmax(pb[0], pb[2]));
+        ad_inv = fmax(ad_inv, fmax(pb[1], pb[3]));
+    }
+    ap_inv = block_max(ap_inv);
+    ad_inv = block_max(ad_inv);
+    if (threadIdx.x == 0) {
+        st->ap = 1.0 / ap_inv;
+        st->ad = 1.0 / ad_inv;
+    }
+}
+
+// Complementarity after the predictor's steps to the boundary: entries into
+// slot 4, nodes into slot 5.
+__global__ void k_ip_comp_aff(int64_t nnz, int64_t n2, const double *f, const double *u, const double *zl,
+                              const double *zh, const double *df, const double *du, const double *dzl,
+                              const double *dzh, const double *p, const double *n, const double *zp, const double *zn,
+                              const double *dp, const double *dn, const double *dzp, const double *dzn,
+                              const IpScalars *st, double *part) {
+    dep_enter();
+    const double ap = st->ap, ad = st->ad;
+    double s = 0.0, t = 0.0;
+    GRID_STRIDE(e, nnz > n2 ? nnz : n2) {
+        if (e < nnz)
+            s += (f[e] + ap * df[e]) * (zl[e] + ad * dzl[e]) + (u[e] + ap * du[e]) * (zh[e] + ad * dzh[e]);
+        if (e < n2)
+            t += (p[e] + ap * dp[e]) * (zp[e] + ad * dzp[e]) + (n[e] + ap * dn[e]) * (zn[e] + ad * dzn[e]);
+    }
+    s = block_sum(s);
+    t = block_sum(t);
+    if (threadIdx.x == 0) {
+        part[kIpSlots * blockIdx.x + 4] = s;
+        part[kIpSlots * blockIdx.x + 5] = t;
+    }
+}
+
+__global__ void k_ip_reduce_comp_aff(const double *part, int nparts, IpScalars *st) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[kIpSlots * k + 4] + part[kIpSlots * k + 5];
+    s = block_sum(s);
+    if (threadIdx.x == 0) st->comp_aff = s;
+}
+
+// Step with fraction 0.99 of the way to the boundary.
+__global__ void k_ip_update(int64_t nnz, int64_t n2, const IpScalars *st, double frac, const double *df,
+                            const double *du, const double *dzl, const double *dzh, const double *dy, const double *dp,
+                            const double *dn, const double *dzp, const double *dzn, double *f, double *u, double *zl,
+                            double *zh, double *y, double *p, double *n, double *zp, double *zn) {
+    dep_enter();
+    const double ap = frac * st->ap, ad = frac * st->ad;
+    GRID_STRIDE(e, nnz > n2 ? nnz : n2) {
+        if (e < nnz) {
+            f[e] += ap * df[e];
+            u[e] += ap * du[e];
+            zl[e] += ad * dzl[e];
+            zh[e] += ad * dzh[e];
+        }
+        if (e < n2) {
+            y[e] += ad * dy[e];
+            p[e] += ap * dp[e];
+            n[e] += ap * dn[e];
+            zp[e] += ad * dzp[e];
+            zn[e] += ad * dzn[e];
+        }
+    }
+}
+
+__global__ void k_ip_init(int64_t nnz, int64_t n2, double *f, double *u, double *zl, double *zh, double *y, double *p,
+                          double *n, double *zp, double *zn) {
+    GRID_STRIDE(e, nnz > n2 ? nnz : n2) {
+        if (e < nnz) {
+            f[e] = 1.0;
+            u[e] = 1.0;
+            zl[e] = 1.0;
+            zh[e] = 1.0;
+        }
+        if (e < n2) {
+            y[e] = 0.0;
+            p[e] = 1.0;
+            n[e] = 1.0;
+            zp[e] = 1.0;
+            zn[e] = 1.0;
+        }
+    }
+}
+
+// x_e = f_e - 1 (kept in qx for the bounds / column-fix stage) and the count
+// of entries within 1e-9 of a bound.
+__global__ void k_ip_finish(int64_t nnz, const double *f, double *qx, DevInfo *info) {
+    int at = 0;
+    GRID_STRIDE(e, nnz) {
+        const double fe = fmin(fmax(f[e], 0.0), 2.0);
+        qx[e] = fe - 1.0;
+        if (fe < 1e-9 || fe > 2.0 - 1e-9) ++at;
+    }
+    if (at) atomicAdd(&info->n_at_bounds, at);
 }
 
 static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res, double *z, const CgState *st,
@@ -490,33 +824,105 @@ static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res,
     }
 }
 
-#ifndef BCHAR_INNER_REDUCTION
-#define BCHAR_INNER_REDUCTION 1e-4
-#endif
-constexpr double kInnerReduction = BCHAR_INNER_REDUCTION;
-constexpr double kFp32Above = 1e-9;  // relative optimality residual above which the V-cycle runs in FP32
-// A round of the conjugate gradients ends when its residual has not dropped
-// by 1 % for kStallIters iterations; the refinement ends when a round that
-// ended so improved the optimality residual by less than a factor of two.
-// Below a floor of about 1e-9..1e-11 of sum |K|_phi (near-null components of
-// the dual, which the operator hardly sees, accumulate in y) the iterations
-// stop making progress, so a tolerance under that floor ends at the floor
-// instead of at qp_max_iter; qp_converged reports whether qp_tol was met.
+// A solve of the conjugate gradients stops when its residual has not dropped
+// by 1 % for kStallIters iterations (it cannot improve further in FP64).
 constexpr int kStallIters = 400;
-// The warm start (see bchar_options.qp_warm_start) begins from zero every
-// kWarmResetSteps steps, so that near-null components cannot pile up in the
-// dual over many steps.
-constexpr int kWarmResetSteps = 32;
-// On 3D meshes the multigrid aggregation is kept for up to kAmgReuseSteps
-// steps (only the level operators are rebuilt from the new matrix), and built
-// anew earlier when a solve needs more than 1.5 times (+5) the iterations of
-// the solve right after the last full build.  3D rows have many entries, the
-// matching is a large part of the set-up, and kept aggregates solved in as
-// few iterations (128^3 porous: 11.3 vs 11.7).  2D meshes build anew every
-// step: their strong row-column pairs move between steps, and kept
-// aggregates raised the iterations from 42 to 363 at 1024^2, while the 2D
-// matching costs a few ms.
-constexpr int kAmgReuseSteps = 8;
+
+// The conjugate gradients on (A-hat D A-hat^T + diag(exc)) d = rhs, from
+// d = 0, until z.res <= target_rz (z the preconditioned residual: about the
+// squared error of d in the norm of the matrix, which bounds the error of
+// A-hat^T d where the interior-point direction needs it -- an L1 test alone
+// would not bound the error along the nearly singular modes of weakly linked
+// cells) and |res|_1 <= target_l1 (the residual feeds the next constraint
+// residual).  One batch of iterations is captured into a CUDA graph
+// per preconditioner build (*exec; destroyed by the caller) and replayed until
+// the solve has converged (its kernels do nothing then); the host polls once
+// per batch.  Returns the iterations done.
+static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double target_rz, double target_l1, bool amg,
+                     bool fp32, int max_iter, cudaGraphExec_t *exec, int *graph_launches) {
+    const int64_t nc = m->nc, n2 = 2 * nc;
+    const int bl = blocks_for(n2);
+    cudaStream_t s = m->stream;
+    double *a2 = ptr<double>(m->a2), *a2c = ptr<double>(m->a2c), *diag = ptr<double>(m->diag);
+    double *d = ptr<double>(m->cg_d), *res = ptr<double>(m->cg_r), *z = ptr<double>(m->cg_z);
+    double *p = ptr<double>(m->cg_p), *q = ptr<double>(m->cg_q), *rp = ptr<double>(m->cg_rp);
+    double *part = ptr<double>(m->partials);
+    double *part_l1 = part + 152 * 64;
+    double *part_rz = part + 2 * 152 * 64;
+    double *part_zp = part + 3 * 152 * 64;
+    CgState *st = ptr<CgState>(m->cg);
+    CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
+    cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
+    k_copy<<<bl, kThreads, 0, s>>>(n2, rhs, res, nullptr);
+    precondition(m, amg, fp32, res, z, nullptr);
+    k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
+    k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, target_rz, target_l1, rhs_l1, st);
+    k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
+    m->launches += 4;
+    const int batch = amg ? 8 : 32;
+    auto enqueue_batch = [&]() {
+        for (int k = 0; k < batch; ++k) {
+            launch_dep(k_cg_matvec, kRedBlocks, kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
+                       ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag, p, q, part, st);
+            launch_dep(k_cg_alpha, 1, 1024, s, part, kRedBlocks, st);
+            if (amg) {
+                if (fp32)
+                    launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, part_l1,
+                               static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
+                else
+                    launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, part_l1,
+                               static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
+                precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
+                m->launches += 3;
+            } else {
+                launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, part_l1, st);
+                precondition(m, amg, fp32, res, z, st);
+                launch_dep(k_dot2, kRedBlocks, kThreads, s, n2, z, res, rp, part_rz, part_zp, st);
+                m->launches += 4;
+            }
+            launch_dep(k_cg_beta, 1, 1024, s, part_rz, part_zp, part_l1, kRedBlocks, st);
+            launch_dep(k_cg_pupdate, bl, kThreads, s, n2, z, p, st);
+            m->launches += 2;
+        }
+    };
+    if (!*exec) {
+        const int before = m->launches;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            enqueue_batch();
+            ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && graph;
+        }
+        if (ok) ok = cudaGraphInstantiate(exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {  // capture unavailable (for instance, the caller is capturing): plain launches
+            cudaGetLastError();
+            *exec = nullptr;
+        }
+        *graph_launches = m->launches - before;
+        m->launches = before;
+    }
+    double best = INFINITY;
+    int best_at = 0;
+    for (;;) {
+        if (*exec) {
+            cudaGraphLaunch(*exec, s);
+            m->launches += *graph_launches;
+        } else {
+            enqueue_batch();
+        }
+        cudaMemcpyAsync(host_st, st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (host_st->converged || host_st->iters >= max_iter) break;
+        if (host_st->res_l1 < 0.99 * best) {
+            best = host_st->res_l1;
+            best_at = host_st->iters;
+        } else if (host_st->iters - best_at >= kStallIters) {
+            break;
+        }
+    }
+    return host_st->iters;
+}
 
 // Host wall clock in milliseconds (for the diagnostic trace only).
 static double trace_ms() {
@@ -525,193 +931,152 @@ static double trace_ms() {
     return t.tv_sec * 1e3 + t.tv_nsec * 1e-6;
 }
 
-void launch_minimise(bchar_mesh_t m, int *cg_iters, int *refines) {
-    const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: residual history and phases on stderr
-    double t_start = 0.0, t_setup = 0.0, t_graph = 0.0;
+// The elastic penalty of the constraints is quadratic up to a relative
+// violation kLinearFrom and linear beyond, with slope gamma = kLinearFrom / eps^2.
+constexpr double kLinearFrom = 1e-6;
+// The interior-point stopping rule: scaled constraint residual <= qp_tol,
+// mean complementarity <= 1e-12, the stationarity residual of 1 + x <= 1e-12 of
+// the largest dual value and those of the violation parts <= 1e-12 of gamma
+// (y and the multipliers reach ~gamma where the problem is infeasible, and the
+// residuals then carry that much rounding).
+constexpr double kIpMuTol = 1e-12;
+// Conjugate-gradient iterations per interior-point solve at most (the late
+// normal equations are badly conditioned; an inexact direction is corrected by
+// the next iteration).
+constexpr int kIpCgPerSolve = 400;
+constexpr double kIpRdRel = 1e-12;
+constexpr double kIpStep = 0.99;
+
+bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
+    const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: per-iteration scalars on stderr
+    double t_start = 0.0;
     if (trace) {
         cudaStreamSynchronize(m->stream);
         t_start = trace_ms();
     }
     const int64_t nc = m->nc, n2 = 2 * nc, nnz = m->nnz;
-    const int bl = blocks_for(n2);
-    const double eps = m->opt.penalty;
+    const size_t zb = sizeof(double) * (nnz > 0 ? nnz : 1), nb = sizeof(double) * n2;
+    Buf *ent[] = {&m->ip_f, &m->ip_u, &m->ip_zl, &m->ip_zh, &m->ip_D, &m->ip_q, &m->ip_cl, &m->ip_ch,
+                  &m->ip_df, &m->ip_du, &m->ip_dzl, &m->ip_dzh};
+    for (Buf *b : ent)
+        if (!ensure(m, *b, zb)) return false;
+    Buf *nod[] = {&m->ip_p, &m->ip_n, &m->ip_zp, &m->ip_zn, &m->ip_cp, &m->ip_cn, &m->ip_dp, &m->ip_dn,
+                  &m->ip_dzp, &m->ip_dzn};
+    for (Buf *b : nod)
+        if (!ensure(m, *b, nb)) return false;
+    static_assert(kIpSlots * kRedBlocks <= 152 * 64, "interior-point partials fit the first scratch section");
     cudaStream_t s = m->stream;
-    double *a2 = ptr<double>(m->a2), *a2c = ptr<double>(m->a2c), *diag = ptr<double>(m->diag);
-    double *rhs = ptr<double>(m->rhs), *qx = ptr<double>(m->qx), *y = ptr<double>(m->qy), *F = ptr<double>(m->F);
-    double *d = ptr<double>(m->cg_d), *res = ptr<double>(m->cg_r), *z = ptr<double>(m->cg_z);
-    double *p = ptr<double>(m->cg_p), *q = ptr<double>(m->cg_q);
+    const double eps2 = m->opt.penalty * m->opt.penalty;
+    const double gamma = kLinearFrom / eps2;
+    const int64_t *row_ptr = ptr<int64_t>(m->row_ptr), *col_ptr = ptr<int64_t>(m->col_ptr);
+    const int32_t *col = ptr<int32_t>(m->col), *csc_src = ptr<int32_t>(m->csc_src);
+    const double *a = ptr<double>(m->aN), *brow = ptr<double>(m->bloc), *volphi = ptr<double>(m->volphi);
+    double *f = ptr<double>(m->ip_f), *u = ptr<double>(m->ip_u), *zl = ptr<double>(m->ip_zl),
+           *zh = ptr<double>(m->ip_zh), *D = ptr<double>(m->ip_D), *q = ptr<double>(m->ip_q),
+           *cl = ptr<double>(m->ip_cl), *ch = ptr<double>(m->ip_ch), *df = ptr<double>(m->ip_df),
+           *du = ptr<double>(m->ip_du), *dzl = ptr<double>(m->ip_dzl), *dzh = ptr<double>(m->ip_dzh);
+    double *p = ptr<double>(m->ip_p), *n = ptr<double>(m->ip_n), *zp = ptr<double>(m->ip_zp),
+           *zn = ptr<double>(m->ip_zn), *cp = ptr<double>(m->ip_cp), *cn = ptr<double>(m->ip_cn),
+           *dp = ptr<double>(m->ip_dp), *dn = ptr<double>(m->ip_dn), *dzp = ptr<double>(m->ip_dzp),
+           *dzn = ptr<double>(m->ip_dzn);
+    double *y = ptr<double>(m->qy), *rp = ptr<double>(m->F), *rhs = ptr<double>(m->rhs), *dy = ptr<double>(m->cg_d);
     double *part = ptr<double>(m->partials);
-    double *part_l1 = part + 152 * 64;
-    double *part_rz = part + 2 * 152 * 64;
-    double *part_zp = part + 3 * 152 * 64;
-    double *rp = ptr<double>(m->cg_rp);
-    DevInfo *di = ptr<DevInfo>(m->dinfo);
-    CgState *st = ptr<CgState>(m->cg);
-    CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
+    IpScalars *st = reinterpret_cast<IpScalars *>(ptr<CgState>(m->cg) + 1);
+    static_assert(sizeof(CgState) + sizeof(IpScalars) <= 256, "both scalar blocks fit the cg buffer");
+    IpScalars hs{};
+    const int blr = kRedBlocks;  // the entry and node passes are grid-stride over kRedBlocks blocks
+    const int bl2 = blocks_for(n2);
+    const int blm = blocks_for(nnz > n2 ? nnz : n2);
+    const double pairs = 2.0 * static_cast<double>(nnz) + 2.0 * static_cast<double>(n2);
+    const bool use_amg = m->opt.qp_precond == 1;
 
-    k_qp_setup<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
-                                      ptr<double>(m->aN), ptr<double>(m->bloc), ptr<double>(m->volphi), eps, a2,
-                                      diag, ptr<double>(m->qexc), rhs);
-    k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, ptr<int32_t>(m->csc_src), a2, a2c);
-    if (m->opt.qp_warm_start && m->have_dual && m->warm_steps < kWarmResetSteps) {
-        ++m->warm_steps;
-        k_qp_warm<<<blocks_for(nc), kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                     ptr<double>(m->aN), y, qx);
-        ++m->launches;
-    } else {
-        cudaMemsetAsync(qx, 0, sizeof(double) * nnz, s);
-        cudaMemsetAsync(y, 0, sizeof(double) * n2, s);
-        m->warm_steps = 0;
-    }
-    m->have_dual = false;  // set again below once this solve has finished
-    m->launches += 2;
-    const bool reuse = m->dim == 3 && m->amg_age >= 0 && m->amg_age < kAmgReuseSteps &&
-                       m->last_cg_iters <= 1.5 * m->amg_built_iters + 5;
-    const bool amg = m->opt.qp_precond == 1 && amg_build(m, m->amg, reuse);
-    m->amg_age = !amg ? -1 : (reuse ? m->amg_age + 1 : 0);
-    if (trace) {
-        cudaStreamSynchronize(m->stream);
-        t_setup = trace_ms();
-        fprintf(stderr, "[bchar] set-up and multigrid %.3f ms (%s)\n", t_setup - t_start, reuse ? "kept aggregates" : "built");
-    }
-    if (trace && amg) {
-        fprintf(stderr, "[bchar] multigrid levels:");
-        for (int l = 0; l < m->amg.nlev; ++l)
-            fprintf(stderr, " %lld/%lld", static_cast<long long>(m->amg.levels[l].n),
-                    static_cast<long long>(m->amg.levels[l].nnz));
-        fprintf(stderr, "\n");
-    }
-
-    int iters = 0, rounds = 0;
-    cudaGraphExec_t exec = nullptr;  // the captured batch, reused by the refinement rounds
-    bool exec_fp32 = true;
-    int graph_launches = 0;
-    const double target_abs = m->opt.qp_tol * total_volphi(m);
-    double kkt = 0.0, prev_kkt = INFINITY;
-    bool stalled = false;
-    for (rounds = 0; rounds <= m->opt.qp_max_refine; ++rounds) {
-        k_qp_kkt<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int64_t>(m->col_ptr),
-                                        ptr<int32_t>(m->csc_src), ptr<double>(m->aN), qx, y, rhs,
-                                        ptr<double>(m->bloc), ptr<double>(m->volphi), eps, F, part);
-        k_sum_partials<<<1, 1024, 0, s>>>(part, bl, &di->kkt_l1);
+    k_ip_init<<<blm, kThreads, 0, s>>>(nnz, n2, f, u, zl, zh, y, p, n, zp, zn);
+    ++m->launches;
+    int it = 0, total_cg = 0;
+    bool converged = false;
+    for (it = 0; it <= m->opt.qp_max_refine; ++it) {
+        launch_dep(k_ip_entries, blr, kThreads, s, nc, row_ptr, col, a, y, f, u, zl, zh, part);
+        launch_dep(k_ip_nodes, blr, kThreads, s, nc, row_ptr, col_ptr, csc_src, a, brow, volphi, eps2, gamma, y, f, p,
+                   n, zp, zn, rp, part);
+        k_ip_reduce_resid<<<1, 1024, 0, s>>>(part, blr, st);
+        m->launches += 3;
+        cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) break;  // the caller reads the error
+        const double mu = hs.comp / pairs;
+        if (trace)
+            fprintf(stderr, "[bchar] ip %d rp %.3e rd %.3e rpq %.3e mu %.3e dual %.3e ap %.3e ad %.3e cg %d (%.1f ms)\n",
+                    it, hs.rp_max, hs.rd_max, hs.rpq_max, mu, hs.dual_max, hs.ap, hs.ad, total_cg,
+                    trace_ms() - t_start);
+        if (hs.rp_max <= m->opt.qp_tol && mu <= kIpMuTol && hs.rd_max <= kIpRdRel * (1.0 + hs.dual_max) &&
+            hs.rpq_max <= kIpRdRel * (1.0 + gamma)) {
+            converged = true;
+            break;
+        }
+        if (it == m->opt.qp_max_refine || total_cg >= m->opt.qp_max_iter) break;
+        // normal-equation matrix and its preconditioner; the weights change by orders of
+        // magnitude between iterations, so the aggregates are built anew every time
+        launch_dep(k_ip_weights, bl2, kThreads, s, nc, row_ptr, col_ptr, csc_src, a, brow, volphi, eps2, f, u, zl, zh, p,
+                   n, zp, zn, D, ptr<double>(m->a2), ptr<double>(m->diag), ptr<double>(m->qexc));
+        k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, csc_src, ptr<double>(m->a2), ptr<double>(m->a2c));
         m->launches += 2;
-        cudaMemcpyAsync(&kkt, &di->kkt_l1, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        if (trace) fprintf(stderr, "[bchar] round %d kkt_l1 %.3e (target %.3e)\n", rounds, kkt, target_abs);
-        if (kkt <= target_abs || rounds == m->opt.qp_max_refine || iters >= m->opt.qp_max_iter) break;
-        if (stalled && kkt > 0.5 * prev_kkt) break;  // the floor: rounds no longer improve
-        prev_kkt = kkt;
-        // restart the conjugate gradients from the true residual once it has
-        // dropped by kInnerReduction: on these ill-conditioned systems short
-        // cycles lose less to round-off than one long one
-        const double inner = fmax(kInnerReduction * kkt, 0.75 * target_abs);
-        cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
-        k_copy<<<bl, kThreads, 0, s>>>(n2, F, res, nullptr);
-        // FP32 V-cycle while the optimality residual is large, FP64 for the last digits
-        const bool fp32 = kkt > kFp32Above * total_volphi(m);
-        if (exec && fp32 != exec_fp32) {
-            cudaGraphExecDestroy(exec);
-            exec = nullptr;
-        }
-        exec_fp32 = fp32;
-        precondition(m, amg, fp32, res, z, nullptr);
-        k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
-        k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, inner, st);
-        k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
-        m->launches += 4;
-        // one batch of iterations is captured once into a CUDA graph and
-        // replayed until the solve converges (its kernels do nothing then)
-        const int batch = amg ? 8 : 32;
-        auto enqueue_batch = [&]() {
-            for (int k = 0; k < batch; ++k) {
-                launch_dep(k_cg_matvec, kRedBlocks, kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                           ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2,
-                                                           a2c, diag, p, q, part, st);
-                launch_dep(k_cg_alpha, 1, 1024, s, part, kRedBlocks, st);
-                if (amg) {
-                    // the update also writes the V-cycle's right-hand side; the
-                    // V-cycle's last kernel also forms the two dot products
-                    if (fp32)
-                        launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, 
-                            nc, p, q, d, res, rp, part_l1, static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
-                    else
-                        launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, 
-                            nc, p, q, d, res, rp, part_l1, static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
-                    precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
-                    m->launches += 3;
-                } else {
-                    launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, part_l1, st);
-                    precondition(m, amg, fp32, res, z, st);
-                    launch_dep(k_dot2, kRedBlocks, kThreads, s, n2, z, res, rp, part_rz, part_zp, st);
-                    m->launches += 4;
-                }
-                launch_dep(k_cg_beta, 1, 1024, s, part_rz, part_zp, part_l1, kRedBlocks, st);
-                launch_dep(k_cg_pupdate, bl, kThreads, s, n2, z, p, st);
+        const bool amg = use_amg && amg_build(m, m->amg, false);
+        // each direction solved until its squared energy-norm error is about <= 1e-2 mu (then
+        // every entry's step error stays about <= 0.1 of its distance to the bound) and its
+        // residual is <= 0.1 of the constraint residual (which the step then reduces), but
+        // not below the rounding of the solve, 1e-12 of sum |K|_phi
+        const double target_rz = 1e-2 * mu;
+        const double target_l1 = fmax(0.1 * hs.rp_l1, 1e-12 * m->sum_volphi);
+        const bool fp32 = mu > 1e-6;
+        cudaGraphExec_t exec = nullptr;
+        int graph_launches = 0;
+        for (int corr = 0; corr < 2; ++corr) {
+            const double sigma_mu = corr ? fmin(1.0, pow(hs.comp_aff / hs.comp, 3.0)) * mu : 0.0;
+            launch_dep(k_ip_q, blr, kThreads, s, nc, row_ptr, col, a, y, f, u, zl, zh, corr, sigma_mu, df, du, dzl,
+                       dzh, cl, ch, q);
+            launch_dep(k_ip_rhs, bl2, kThreads, s, nc, row_ptr, col_ptr, csc_src, a, D, q, rp, brow, volphi, gamma, y,
+                       p, n, zp, zn, corr, sigma_mu, dp, dn, dzp, dzn, cp, cn, rhs);
+            m->launches += 2;
+            const int left = m->opt.qp_max_iter - total_cg;
+            const int cap = left < kIpCgPerSolve ? left : kIpCgPerSolve;
+            // the right-hand side's L1 norm: the node pass's |rp|_1 bounds it well enough for the start
+            total_cg += pcg_solve(m, rhs, hs.rp_l1, target_rz, target_l1, amg, fp32 && amg, cap > 0 ? cap : 1,
+                                  &exec, &graph_launches);
+            launch_dep(k_ip_dir, blr, kThreads, s, nc, row_ptr, col, a, dy, f, u, zl, zh, D, q, cl, ch, df, du, dzl,
+                       dzh, part);
+            launch_dep(k_ip_dir_nodes, blr, kThreads, s, nc, brow, volphi, gamma, y, dy, p, n, zp, zn, cp, cn, dp, dn,
+                       dzp, dzn, part);
+            k_ip_reduce_steps<<<1, 1024, 0, s>>>(part, blr, st);
+            m->launches += 3;
+            if (!corr) {
+                launch_dep(k_ip_comp_aff, blr, kThreads, s, nnz, n2, f, u, zl, zh, df, du, dzl, dzh, p, n, zp, zn, dp,
+                           dn, dzp, dzn, st, part);
+                k_ip_reduce_comp_aff<<<1, 1024, 0, s>>>(part, blr, st);
                 m->launches += 2;
-            }
-        };
-        if (!exec) {
-            const double t0 = trace ? trace_ms() : 0.0;
-            const int before = m->launches;
-            cudaGraph_t graph = nullptr;
-            bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            if (ok) {
-                enqueue_batch();
-                ok = cudaStreamEndCapture(s, &graph) == cudaSuccess && graph;
-            }
-            if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-            if (graph) cudaGraphDestroy(graph);
-            if (!ok) {  // capture unavailable (for instance, the caller is capturing): plain launches
-                cudaGetLastError();
-                exec = nullptr;
-            }
-            graph_launches = m->launches - before;
-            m->launches = before;
-            if (trace) t_graph += trace_ms() - t0;
-        }
-        int done = 0;
-        double best = INFINITY;
-        int best_at = 0;
-        stalled = false;
-        while (!done) {
-            if (exec) {
-                cudaGraphLaunch(exec, s);
-                m->launches += graph_launches;
-            } else {
-                enqueue_batch();
-            }
-            cudaMemcpyAsync(host_st, st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            if (trace && (host_st->iters % 512 < batch || host_st->converged))
-                fprintf(stderr, "[bchar] round %d iter %d res_l1 %.3e target %.3e\n", rounds, host_st->iters,
-                        host_st->res_l1, host_st->target);
-            if (host_st->converged || iters + host_st->iters >= m->opt.qp_max_iter) done = 1;
-            if (host_st->res_l1 < 0.99 * best) {
-                best = host_st->res_l1;
-                best_at = host_st->iters;
-            } else if (host_st->iters - best_at >= kStallIters) {
-                stalled = true;
-                done = 1;
+                cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s);
+                cudaStreamSynchronize(s);
             }
         }
-        iters += host_st->iters;
-        k_qp_accumulate<<<bl, kThreads, 0, s>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                               ptr<double>(m->aN), d, qx, y);
+        if (exec) cudaGraphExecDestroy(exec);
+        launch_dep(k_ip_update, blm, kThreads, s, nnz, n2, st, kIpStep, df, du, dzl, dzh, dy, dp, dn, dzp, dzn, f, u,
+                   zl, zh, y, p, n, zp, zn);
         ++m->launches;
     }
-    if (exec) cudaGraphExecDestroy(exec);
+    k_ip_finish<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, f, ptr<double>(m->qx), ptr<DevInfo>(m->dinfo));
+    ++m->launches;
+    DevInfo *di = ptr<DevInfo>(m->dinfo);
+    cudaMemcpyAsync(&di->kkt_l1, &st->rp_max, sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (trace) {
-        cudaStreamSynchronize(m->stream);
-        fprintf(stderr, "[bchar] capture+instantiate %.3f ms, total %.3f ms, %d iterations\n", t_graph,
-                trace_ms() - t_start, iters);
+        cudaStreamSynchronize(s);
+        fprintf(stderr, "[bchar] interior point: %d iterations, %d CG iterations, %s, %.3f ms\n", it, total_cg,
+                converged ? "converged" : "not converged", trace_ms() - t_start);
     }
-    m->have_dual = isfinite(kkt);
-    if (m->amg_age == 0) m->amg_built_iters = iters;
-    m->last_cg_iters = iters;
-    *cg_iters = iters;
-    *refines = rounds;
-    m->amg_levels = amg ? m->amg.nlev : 0;
-    m->amg_coarsest = amg ? m->amg.levels[m->amg.nlev - 1].n : 0;
+    m->ip_iters = it;
+    m->ip_converged = converged;
+    *cg_iters = total_cg;
+    *ip_iters = it;
+    m->amg_levels = use_amg ? m->amg.nlev : 0;
+    m->amg_coarsest = use_amg && m->amg.nlev > 0 ? m->amg.levels[m->amg.nlev - 1].n : 0;
+    return true;
 }
 
 void launch_cg_matvec_once(bchar_mesh_t m, CgState *st) {
@@ -724,23 +1089,15 @@ void launch_cg_matvec_once(bchar_mesh_t m, CgState *st) {
 
 // ---------------------------------------------------------------- bounds, column fix, W
 
-// a_q = a^(N) clip(1 + x, 0, 2), per row; counts entries outside the bounds.
-__global__ void k_clip(int64_t nc, const int64_t *row_ptr, const double *aN, const double *qx, double *aq,
-                       DevInfo *info) {
-    int clipped = 0;
+// a_q = a^(N) (1 + x), per row (1 + x is inside [0, 2] by construction).
+__global__ void k_clip(int64_t nc, const int64_t *row_ptr, const double *aN, const double *qx, double *aq) {
     GRID_STRIDE(i, nc) {
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            double f = 1.0 + qx[e];
-            if (f < 0.0 || f > 2.0) ++clipped;
-            f = fmin(fmax(f, 0.0), 2.0);
-            aq[e] = aN[e] * f;
-        }
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) aq[e] = aN[e] * fmin(fmax(1.0 + qx[e], 0.0), 2.0);
     }
-    if (clipped) atomicAdd(&info->n_clipped, clipped);
 }
 
 // C2_j = |M_j|_phi / sum_i a_q,ij (first half of eq. volAdj).  A column whose
-// entries were all clipped to zero keeps its A^(N) entries (dead[j] = 1).
+// entries all ended on the bound 0 keeps its A^(N) entries (dead[j] = 1).
 __global__ void k_colfix(int64_t nc, const int64_t *col_ptr, const int32_t *csc_src, const double *aq,
                          const double *aN, const double *volphi, double *C2, int32_t *dead) {
     GRID_STRIDE(j, nc) {
@@ -782,7 +1139,7 @@ void launch_finalise(bchar_mesh_t m) {
     const int bl = blocks_for(nc);
     DevInfo *di = ptr<DevInfo>(m->dinfo);
     double *aq = ptr<double>(m->a2);  // reuse: a2 is no longer needed
-    k_clip<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<double>(m->aN), ptr<double>(m->qx), aq, di);
+    k_clip<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<double>(m->aN), ptr<double>(m->qx), aq);
     int32_t *dead = ptr<int32_t>(m->colfill);  // scratch: the column fill counters are no longer needed
     k_colfix<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src), aq,
                                              ptr<double>(m->aN), ptr<double>(m->volphi), ptr<double>(m->C), dead);

@@ -35,7 +35,7 @@ def test_binding_marshals_options_and_status_strings():
     from paper_1908_05834_gb300 import bchar
     o = bchar.default_options()
     assert (o.balls_per_axis, o.n_scale, o.precision) == (2, 10, bchar.FP64)
-    assert o.penalty == pytest.approx(1e-7) and o.qp_tol == pytest.approx(1e-14)
+    assert o.penalty == pytest.approx(1e-7) and o.qp_tol == pytest.approx(1e-9)
     # the last fields: a mismatch between the ctypes mirror and the header would show here
     assert (o.qp_precond, o.qp_warm_start) == (1, 1)
     assert bchar.bchar_status_string(0) == b"ok"

@@ -74,6 +74,8 @@ typedef struct {
                            1 = aggregation multigrid (default), 0 = Jacobi */
     int qp_warm_start;  /* reserved (0 or 1, default 1): every minimisation starts from
                            1 + x = 1 with unit bound multipliers and zero constraint multipliers */
+    int slab_width;     /* entries per row of the assembly's row slab; 0 (default) = 24 in 2D,
+                           64 in 3D; wider rows go to the spill area (results are the same) */
 } bchar_options;
 
 typedef struct {
@@ -96,9 +98,11 @@ typedef struct {
     int32_t amg_levels;      /* levels of the multigrid preconditioner (0 = Jacobi) */
     int32_t amg_coarsest;    /* unknowns on its coarsest level */
     int32_t unbalanced;      /* connected components whose local targets were rescaled (see bchar_step) */
-    int32_t row_cap;         /* entries per row of the assembly's row slab: 24 (2D) or 64 (3D), grown to
-                              * the widest row (rounded up to 8) when a row did not fit; it never
-                              * shrinks, and the slab holds n_c x row_cap x 12 bytes */
+    int32_t row_cap;         /* entries per row of the assembly's row slab: 24 (2D) or 64 (3D); the slab
+                              * holds n_c x row_cap x 12 bytes */
+    int32_t spill_rows;      /* rows wider than the slab, assembled a second time into a spill area of
+                              * their exact total length */
+    int32_t max_row_len;     /* entries of the widest row of A */
     /* Milliseconds on the handle's stream (CUDA events) per stage of this call:
      * [0] tracking, [1] intersections and row assembly (with empty-column
      * seeding), [2] compaction, column view and target balancing, [3] the N
@@ -204,14 +208,16 @@ enum {
     BCHAR_STAGE_UPDATE = 1,    /* c^{n+1} = W c^n and the mass sums */
     BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
     BCHAR_STAGE_TRACK = 3,     /* RK4 tracking of all balls */
-    BCHAR_STAGE_SMOOTH = 4     /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
+    BCHAR_STAGE_SMOOTH = 4,    /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
+    BCHAR_STAGE_SCALING = 5    /* one column and one row scaling of eq. volAdj (on scratch copies) */
 };
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of
  * the last step, on the handle's stream, and return the mean duration of one
  * launch in milliseconds (CUDA events around the replays).  CG_MATVEC, UPDATE
  * and SMOOTH are replayed from one CUDA graph of `reps` launches (captured on a
- * private stream), so that host launch overhead is not measured.  The replays do
+ * private stream), so that host launch overhead is not measured; SCALING too
+ * (it writes the scaling factors, which the step no longer needs).  The replays do
  * not change the result of the last step (exports stay valid) except that
  * BCHAR_STAGE_TRACK overwrites the tracked balls with the same values.
  * Errors: INVALID_ARG (no step yet, bad stage, reps < 1), CUDA. */
@@ -257,10 +263,10 @@ bchar_status bchar_device_bytes(bchar_mesh_t m, int64_t *now, int64_t *peak);
  * allocation: per cell (mesh arrays, minimisation vectors, row slab,
  * multigrid), per ball (the tight packing, counted here from the widths)
  * and per matrix entry, with the entries bounded by a 3^d neighbourhood per
- * row (9 in 2D, 27 in 3D), plus 10 %.  A step whose rows grow wider than the
- * slab's initial capacity (24 entries in 2D, 64 in 3D) holds more: about
- * n_c x 12 x (row_cap - initial capacity) bytes, with row_cap as reported in
- * bchar_step_info.  Host only; no GPU work.  coords as for bchar_create_mesh; opt NULL = defaults.
+ * row (9 in 2D, 27 in 3D), plus 10 %.  Rows wider than the slab's 24 (2D)
+ * or 64 (3D) entries are held at their exact length in a spill area, which the
+ * per-entry count covers.  Host only; no GPU work.  coords as for
+ * bchar_create_mesh; opt NULL = defaults.
  * Errors: INVALID_ARG. */
 bchar_status bchar_estimate_device_bytes(int dim, const int64_t n_cells[3], const double *const coords[3],
                                          const bchar_options *opt, int64_t *bytes);

@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
                 ("substeps", ctypes.c_int), ("cfl", ctypes.c_double), ("drop_tol", ctypes.c_double),
                 ("penalty", ctypes.c_double), ("qp_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int),
                 ("qp_max_refine", ctypes.c_int), ("div_tol", ctypes.c_double), ("qp_precond", ctypes.c_int),
-                ("qp_warm_start", ctypes.c_int)]
+                ("qp_warm_start", ctypes.c_int), ("slab_width", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -40,7 +40,7 @@ class StepInfo(ctypes.Structure):
                 ("ip_iters", ctypes.c_int32), ("qp_converged", ctypes.c_int32), ("void_balls", ctypes.c_int32),
                 ("empty_cols", ctypes.c_int32), ("n_at_bounds", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("amg_levels", ctypes.c_int32), ("amg_coarsest", ctypes.c_int32), ("unbalanced", ctypes.c_int32),
-                ("row_cap", ctypes.c_int32),
+                ("row_cap", ctypes.c_int32), ("spill_rows", ctypes.c_int32), ("max_row_len", ctypes.c_int32),
                 ("ms_stage", ctypes.c_float * 8)]
 
     STAGES = ("track", "assemble", "columns_balance", "scaling", "minimise", "finalise", "update", "total")
@@ -92,7 +92,7 @@ lib.bchar_export_tracked.restype = ctypes.c_int
 lib.bchar_time_stage.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
 lib.bchar_time_stage.restype = ctypes.c_int
 
-STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK, STAGE_SMOOTH = 0, 1, 2, 3, 4
+STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK, STAGE_SMOOTH, STAGE_SCALING = 0, 1, 2, 3, 4, 5
 
 lib.bchar_mass_noalloc.argtypes = [_P, _P, ctypes.c_int, _I64, _P, _P]
 lib.bchar_mass_noalloc.restype = ctypes.c_int

@@ -10,6 +10,10 @@
 // sums its denominator; then the lanes sweep the union box of the cell, one
 // residing cell M per lane, and the non-zero V_{K,M} (>= drop_tol |K|_phi)
 // are compacted into the row with a warp ballot, in increasing column order.
+// Rows are written to a slab of row_cap entries per row; a row with more
+// entries records its length only, and a second pass over those rows alone
+// writes them, at their exact length, to a spill area (offsets from a scan),
+// so memory follows the number of non-zeros rather than the widest row.
 // A tracked ball that meets no residing ball gives its whole mass to the cell
 // holding its centre.
 //
@@ -124,7 +128,9 @@ template <class real, int DIM>
 __global__ void __launch_bounds__(256, 3) k_assemble(MeshView m, const int32_t *t_cell, const real *t_xi,
                                                   const real *t_rhat, double drop_tol, int row_cap, int win_cap,
                                                   int32_t *slab_col, double *slab_val, int32_t *row_len,
+                                                  const int64_t *spill_off, int32_t *spill_col, double *spill_val,
                                                   DevInfo *info) {
+    const bool spill = spill_col != nullptr;  // second pass: only the rows wider than the slab
     __shared__ BallSmem<real> sm_all[256 / 32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -132,6 +138,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble(MeshView m, const int32_t *
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     const real r_max = static_cast<real>(m.r_max);
     for (int64_t K = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + wib; K < m.nc; K += nwarps) {
+        if (spill && row_len[K] <= row_cap) continue;  // warp-uniform
         const int64_t off = m.ball_off[K];
         const int nK = static_cast<int>(m.ball_off[K + 1] - off);
         if (nK > kMaxBallsPerCell) {  // warp-uniform
@@ -267,18 +274,19 @@ __global__ void __launch_bounds__(256, 3) k_assemble(MeshView m, const int32_t *
             const bool keep = t < nW && V > 0.0 && V >= thr;
             const unsigned mask = __ballot_sync(0xffffffffu, keep);
             const int pos = count + __popc(mask & ((1u << lane) - 1u));
-            if (keep && pos < row_cap) {
+            if (keep && spill) {
+                spill_col[spill_off[K] + pos] = static_cast<int32_t>(M);
+                spill_val[spill_off[K] + pos] = V;
+            } else if (keep && pos < row_cap) {
                 slab_col[K * row_cap + pos] = static_cast<int32_t>(M);
                 slab_val[K * row_cap + pos] = V;
             }
             count += __popc(mask);
         }
-        if (lane == 0) {
-            row_len[K] = min(count, row_cap);
-            if (count > row_cap) {
-                atomicMax(&info->need_row_cap, count);
-                atomicOr(&info->err, kErrRowCapacity);
-            }
+        if (lane == 0 && !spill) {
+            row_len[K] = count;  // the true length; rows wider than the slab are written by the spill pass
+            atomicMax(&info->need_row_cap, count);
+            if (count > row_cap) atomicAdd(&info->n_spill_rows, 1);
         }
         __syncwarp();
     }
@@ -287,45 +295,81 @@ __global__ void __launch_bounds__(256, 3) k_assemble(MeshView m, const int32_t *
 MeshView full_view(bchar_mesh_t m);
 
 template <class real, int DIM>
-static void assemble_in(bchar_mesh_t m, const MeshView &mv, int win_cap, int blocks) {
-    k_assemble<real, DIM><<<blocks, 256, 0, m->stream>>>(mv, ptr<int32_t>(m->t_cell), ptr<real>(m->t_xi),
-                                                         ptr<real>(m->t_rhat), m->opt.drop_tol, m->row_cap, win_cap,
-                                                         ptr<int32_t>(m->slab_col), ptr<double>(m->slab_val),
-                                                         ptr<int32_t>(m->row_len), ptr<DevInfo>(m->dinfo));
+static void assemble_in(bchar_mesh_t m, const MeshView &mv, int win_cap, int blocks, bool spill) {
+    k_assemble<real, DIM><<<blocks, 256, 0, m->stream>>>(
+        mv, ptr<int32_t>(m->t_cell), ptr<real>(m->t_xi), ptr<real>(m->t_rhat), m->opt.drop_tol, m->row_cap, win_cap,
+        ptr<int32_t>(m->slab_col), ptr<double>(m->slab_val), ptr<int32_t>(m->row_len),
+        spill ? ptr<int64_t>(m->spill_off) : nullptr, spill ? ptr<int32_t>(m->spill_col) : nullptr,
+        spill ? ptr<double>(m->spill_val) : nullptr, ptr<DevInfo>(m->dinfo));
 }
 
-void launch_assemble(bchar_mesh_t m) {
+static void assemble_pass(bchar_mesh_t m, bool spill) {
     MeshView mv = full_view(m);
     const int win_cap = m->dim == 2 ? 4096 : 32768;
     const int blocks = blocks_for(m->nc * 32, 256);
     const bool f32 = m->opt.precision == BCHAR_FP32_SPLIT;
     if (m->dim == 2) {
         if (f32)
-            assemble_in<float, 2>(m, mv, win_cap, blocks);
+            assemble_in<float, 2>(m, mv, win_cap, blocks, spill);
         else
-            assemble_in<double, 2>(m, mv, win_cap, blocks);
+            assemble_in<double, 2>(m, mv, win_cap, blocks, spill);
     } else {
         if (f32)
-            assemble_in<float, 3>(m, mv, win_cap, blocks);
+            assemble_in<float, 3>(m, mv, win_cap, blocks, spill);
         else
-            assemble_in<double, 3>(m, mv, win_cap, blocks);
+            assemble_in<double, 3>(m, mv, win_cap, blocks, spill);
     }
     ++m->launches;
+}
+
+void launch_assemble(bchar_mesh_t m) { assemble_pass(m, false); }
+
+__global__ void k_spill_counts(int64_t nc, int row_cap, const int32_t *row_len, int32_t *cnt) {
+    for (int64_t K = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; K < nc;
+         K += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        cnt[K] = row_len[K] > row_cap ? row_len[K] : 0;
+}
+
+bool launch_assemble_spill(bchar_mesh_t m) {
+    if (!ensure(m, m->spill_cnt, sizeof(int32_t) * m->nc) || !ensure(m, m->spill_off, sizeof(int64_t) * (m->nc + 1)))
+        return false;
+    k_spill_counts<<<blocks_for(m->nc), kThreads, 0, m->stream>>>(m->nc, m->row_cap, ptr<int32_t>(m->row_len),
+                                                                  ptr<int32_t>(m->spill_cnt));
+    ++m->launches;
+    scan_i32_to_i64(m, ptr<int32_t>(m->spill_cnt), ptr<int64_t>(m->spill_off), m->nc);
+    int64_t total = 0;
+    cudaMemcpyAsync(&total, ptr<int64_t>(m->spill_off) + m->nc, sizeof total, cudaMemcpyDeviceToHost, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return true;  // the caller reads the error
+    const size_t z = total > 0 ? static_cast<size_t>(total) : 1;
+    if (!ensure(m, m->spill_col, sizeof(int32_t) * z) || !ensure(m, m->spill_val, sizeof(double) * z)) return false;
+    assemble_pass(m, true);
+    return true;
+}
+
+// Where row K's entries are: the slab, or the spill area when it is wider.
+__device__ __forceinline__ int64_t row_src(int64_t K, int row_cap, int32_t len, const int64_t *spill_off) {
+    return len > row_cap ? -1 - spill_off[K] : K * row_cap;
 }
 
 // ---------------------------------------------------------------- columns
 
 __global__ void k_column_counts(int64_t nc, int row_cap, const int32_t *row_len, const int32_t *slab_col,
-                                int32_t *colcnt) {
+                                const int64_t *spill_off, const int32_t *spill_col, int32_t *colcnt) {
     for (int64_t K = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; K < nc;
-         K += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        for (int e = 0; e < row_len[K]; ++e) atomicAdd(&colcnt[slab_col[K * row_cap + e]], 1);
+         K += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t len = row_len[K];
+        const int64_t src = row_src(K, row_cap, len, spill_off);
+        const int32_t *cols = src >= 0 ? slab_col + src : spill_col + (-1 - src);
+        for (int e = 0; e < len; ++e) atomicAdd(&colcnt[cols[e]], 1);
+    }
 }
 
 void launch_column_counts(bchar_mesh_t m) {
     cudaMemsetAsync(m->colcnt.p, 0, sizeof(int32_t) * m->nc, m->stream);
-    k_column_counts<<<blocks_for(m->nc), kThreads, 0, m->stream>>>(m->nc, m->row_cap, ptr<int32_t>(m->row_len),
-                                                                   ptr<int32_t>(m->slab_col), ptr<int32_t>(m->colcnt));
+    const bool sp = m->spill_rows > 0;
+    k_column_counts<<<blocks_for(m->nc), kThreads, 0, m->stream>>>(
+        m->nc, m->row_cap, ptr<int32_t>(m->row_len), ptr<int32_t>(m->slab_col), sp ? ptr<int64_t>(m->spill_off) : nullptr,
+        sp ? ptr<int32_t>(m->spill_col) : nullptr, ptr<int32_t>(m->colcnt));
     ++m->launches;
 }
 
@@ -366,7 +410,7 @@ __global__ void k_insert_seeds(int64_t nc, int row_cap, const unsigned long long
         const int64_t row = static_cast<int64_t>(seeds[i] >> 32);
         if (i > 0 && static_cast<int64_t>(seeds[i - 1] >> 32) == row) continue;  // first seed of its row does the row
         int e = i;
-        int len = row_len[row];
+        int len = row_len[row];  // a row in the spill area (len > row_cap) is refused below
         while (e < nseeds && static_cast<int64_t>(seeds[e] >> 32) == row) {
             const int32_t col = static_cast<int32_t>(seeds[e] & 0xffffffffull);
             if (len >= row_cap) {
@@ -397,24 +441,30 @@ void launch_insert_seeds(bchar_mesh_t m, int nseeds) {
     m->launches += 2;
 }
 
-// Slab rows -> CSR (row_ptr from the scan of the row lengths).
+// Slab and spill rows -> CSR (row_ptr from the scan of the row lengths).
 __global__ void k_compact(int64_t nc, int row_cap, const int32_t *row_len, const int64_t *row_ptr,
-                          const int32_t *slab_col, const double *slab_val, int32_t *col, double *val) {
+                          const int32_t *slab_col, const double *slab_val, const int64_t *spill_off,
+                          const int32_t *spill_col, const double *spill_val, int32_t *col, double *val) {
     for (int64_t K = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; K < nc;
          K += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t dst = row_ptr[K];
-        for (int e = 0; e < row_len[K]; ++e) {
-            col[dst + e] = slab_col[K * row_cap + e];
-            val[dst + e] = slab_val[K * row_cap + e];
+        const int32_t len = row_len[K];
+        const int64_t src = row_src(K, row_cap, len, spill_off);
+        const int32_t *cs = src >= 0 ? slab_col + src : spill_col + (-1 - src);
+        const double *vs = src >= 0 ? slab_val + src : spill_val + (-1 - src);
+        for (int e = 0; e < len; ++e) {
+            col[dst + e] = cs[e];
+            val[dst + e] = vs[e];
         }
     }
 }
 
 void launch_compact(bchar_mesh_t m) {
-    k_compact<<<blocks_for(m->nc), kThreads, 0, m->stream>>>(m->nc, m->row_cap, ptr<int32_t>(m->row_len),
-                                                             ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->slab_col),
-                                                             ptr<double>(m->slab_val), ptr<int32_t>(m->col),
-                                                             ptr<double>(m->a0));
+    const bool sp = m->spill_rows > 0;
+    k_compact<<<blocks_for(m->nc), kThreads, 0, m->stream>>>(
+        m->nc, m->row_cap, ptr<int32_t>(m->row_len), ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->slab_col),
+        ptr<double>(m->slab_val), sp ? ptr<int64_t>(m->spill_off) : nullptr, sp ? ptr<int32_t>(m->spill_col) : nullptr,
+        sp ? ptr<double>(m->spill_val) : nullptr, ptr<int32_t>(m->col), ptr<double>(m->a0));
     ++m->launches;
 }
 

@@ -116,7 +116,7 @@ bool options_valid(const bchar_options &o) {
            (o.precision == BCHAR_FP64 || o.precision == BCHAR_FP32_SPLIT) && o.substeps >= 0 && o.cfl > 0.0 &&
            o.drop_tol >= 0.0 && o.drop_tol < 1.0 && o.penalty > 0.0 && o.qp_tol > 0.0 && o.qp_max_iter >= 0 &&
            o.qp_max_refine >= 0 && o.div_tol > 0.0 && (o.qp_precond == 0 || o.qp_precond == 1) &&
-           (o.qp_warm_start == 0 || o.qp_warm_start == 1);
+           (o.qp_warm_start == 0 || o.qp_warm_start == 1) && o.slab_width >= 0 && o.slab_width <= 4096;
 }
 
 }  // namespace
@@ -138,6 +138,7 @@ void bchar_default_options(bchar_options *o) {
     o->div_tol = 1e-9;
     o->qp_precond = 1;
     o->qp_warm_start = 1;
+    o->slab_width = 0;
 }
 
 const char *bchar_status_string(bchar_status s) {
@@ -166,7 +167,7 @@ void bchar_destroy(bchar_mesh_t m) {
     Buf *all[] = {&m->phi, &m->phif, &m->volphi, &m->rad, &m->radf, &m->rhophi, &m->rhophif, &m->cnt,
                   &m->ball_off, &m->ball_cell, &m->t_cell, &m->t_xi, &m->t_rhat, &m->slab_col, &m->slab_val,
                   &m->row_len, &m->colcnt, &m->colfill, &m->seeds, &m->seed_row_cnt, &m->row_ptr, &m->col_ptr,
-                  &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->bloc, &m->uf_parent, &m->uf_label, &m->comp_acc, &m->a2,
+                  &m->col, &m->a0, &m->aN, &m->afin, &m->wgt, &m->csc_row, &m->csc_src, &m->R, &m->C, &m->bloc, &m->tile_r, &m->tile_c, &m->uf_parent, &m->uf_label, &m->comp_acc, &m->a2,
                   &m->a2c, &m->diag, &m->qexc, &m->rhs, &m->qx, &m->qy, &m->F, &m->cg_d, &m->cg_r, &m->cg_z, &m->cg_p,
                   &m->cg_q, &m->cg_rp, &m->scan_tmp, &m->partials, &m->dinfo, &m->cg, &m->ip_f, &m->ip_u,
                   &m->ip_zl, &m->ip_zh, &m->ip_D, &m->ip_q, &m->ip_cl, &m->ip_ch, &m->ip_df, &m->ip_du,
@@ -312,7 +313,7 @@ bchar_status bchar_create_mesh(int dim, const int64_t *n_cells, const double *co
     const size_t rb = o.precision == BCHAR_FP32_SPLIT ? sizeof(float) : sizeof(double);
     ok = ensure(m, m->ball_cell, sizeof(int32_t) * nballs) && ensure(m, m->t_cell, sizeof(int32_t) * nballs) &&
          ensure(m, m->t_xi, rb * 3 * nballs) && ensure(m, m->t_rhat, rb * nballs);
-    m->row_cap = dim == 2 ? 24 : 64;
+    m->row_cap = o.slab_width > 0 ? o.slab_width : (dim == 2 ? 24 : 64);
     ok = ok && ensure(m, m->slab_col, sizeof(int32_t) * nc * m->row_cap) &&
          ensure(m, m->slab_val, sizeof(double) * nc * m->row_cap);
     if (!ok) {
@@ -406,25 +407,16 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
     launch_track(m, dt, substeps);
     cudaEventRecord(ev[1], m->stream);
 
-    // initial weights, row by row, into the slab; grow the slab if a row is wider
+    // initial weights, row by row, into the slab; rows wider than the slab go to the spill area
     DevInfo *h = host_info(m);
     bchar_status st;
-    for (int attempt = 0;; ++attempt) {
-        launch_assemble(m);
-        launch_column_counts(m);
-        launch_seed_columns(m, dt, substeps);
-        if ((st = read_info(m)) != BCHAR_OK) return st;
-        if ((h->err & kErrRowCapacity) && attempt < 2) {
-            int cap = (h->need_row_cap + 7) / 8 * 8;
-            if (!ensure(m, m->slab_col, sizeof(int32_t) * m->nc * cap) ||
-                !ensure(m, m->slab_val, sizeof(double) * m->nc * cap))
-                return BCHAR_ERR_OUT_OF_MEMORY;
-            m->row_cap = cap;
-            cudaMemsetAsync(m->dinfo.p, 0, sizeof(DevInfo), m->stream);
-            continue;
-        }
-        break;
-    }
+    launch_assemble(m);
+    if ((st = read_info(m)) != BCHAR_OK) return st;
+    m->spill_rows = h->n_spill_rows;
+    if (m->spill_rows > 0 && !launch_assemble_spill(m)) return BCHAR_ERR_OUT_OF_MEMORY;
+    launch_column_counts(m);
+    launch_seed_columns(m, dt, substeps);
+    if ((st = read_info(m)) != BCHAR_OK) return st;
     if (h->err) {
         char msg[96];
         snprintf(msg, sizeof msg, "capacity error bits 0x%x during assembly", h->err);
@@ -455,6 +447,7 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         return BCHAR_ERR_OUT_OF_MEMORY;
     launch_compact(m);
     launch_transpose(m);
+    if (!launch_tiles(m)) return BCHAR_ERR_OUT_OF_MEMORY;
     if (!launch_balance(m)) return BCHAR_ERR_OUT_OF_MEMORY;
     cudaEventRecord(ev[3], m->stream);
 
@@ -501,6 +494,8 @@ bchar_status bchar_step(bchar_mesh_t m, double dt, const void *c_in, void *c_out
         info->amg_levels = m->amg_levels;
         info->amg_coarsest = static_cast<int32_t>(m->amg_coarsest);
         info->row_cap = m->row_cap;
+        info->spill_rows = m->spill_rows;
+        info->max_row_len = h->need_row_cap;
         info->unbalanced = h->unbalanced;
         for (int k = 0; k < 8; ++k) info->ms_stage[k] = ms_stage[k];
     }
@@ -585,12 +580,14 @@ bchar_status bchar_estimate_device_bytes(int dim, const int64_t *n_cells, const 
     // mesh and row arrays 116, minimisation vectors 2 x 11 x 8, union-find 80,
     // face velocities 12 d, tracking records kRecordLen x precision, row slab
     // 12 row_cap, matching scratch 48, multigrid level 0 144 and coarser levels
-    // ~154; per entry: CSR and column view 68, multigrid level 0 48 and coarser
-    // ~50; per ball 8 + 4 (3 + 1) x precision.
-    const int row_cap = dim == 2 ? 24 : 64;
+    // ~154, interior-point state of the 2 constraint nodes 2 x 10 x 8, spill
+    // counts and offsets 12; per entry: CSR and column view 68, multigrid
+    // level 0 48 and coarser ~50, interior-point state 12 x 8, spill area at
+    // most 12; per ball 8 + 4 (3 + 1) x precision.
+    const int row_cap = o.slab_width > 0 ? o.slab_width : (dim == 2 ? 24 : 64);
     const double rec = kRecordLen * (o.precision == BCHAR_FP32_SPLIT ? 4.0 : 8.0);
-    const double per_cell = 116 + 176 + 80 + 12.0 * dim + rec + 12.0 * row_cap + 48 + 144 + 154;
-    const double per_entry = 68 + 48 + 50;
+    const double per_cell = 116 + 176 + 80 + 12.0 * dim + rec + 12.0 * row_cap + 48 + 144 + 154 + 160 + 12;
+    const double per_entry = 68 + 48 + 50 + 96 + 12;
     const double per_ball = 8 + 4.0 * (o.precision == BCHAR_FP32_SPLIT ? 4 : 8);
     const double nnz_bound = (dim == 2 ? 9.0 : 27.0) * nc;  // a 3^d neighbourhood per row
     const double fixed = 4.0 * 152 * 64 * 8 + 4096 * 8 + (1 << 20);
@@ -600,7 +597,7 @@ bchar_status bchar_estimate_device_bytes(int dim, const int64_t *n_cells, const 
 
 bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms) {
     if (!m) return BCHAR_ERR_INVALID_ARG;
-    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 4 ||
+    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 5 ||
         (stage == BCHAR_STAGE_SMOOTH && m->amg_levels == 0))
         return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet or bad arguments");
     Buf st, cin, cout;
@@ -620,6 +617,7 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
         case BCHAR_STAGE_UPDATE: launch_update(m, cin.p, cout.p, BCHAR_C_F64); break;
         case BCHAR_STAGE_ASSEMBLE: launch_assemble(m); break;
         case BCHAR_STAGE_SMOOTH: amg_smooth_once(m, m->amg); break;
+        case BCHAR_STAGE_SCALING: launch_scaling_once(m); break;
         default: launch_track(m, m->dt, m->substeps); break;
         }
     };
@@ -628,7 +626,8 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
     // so that the host's launch rate does not bound the measurement; the
     // graph is captured on a private stream and launched on the handle's.
     cudaGraphExec_t exec = nullptr;
-    if (stage == BCHAR_STAGE_CG_MATVEC || stage == BCHAR_STAGE_UPDATE || stage == BCHAR_STAGE_SMOOTH) {
+    if (stage == BCHAR_STAGE_CG_MATVEC || stage == BCHAR_STAGE_UPDATE || stage == BCHAR_STAGE_SMOOTH ||
+        stage == BCHAR_STAGE_SCALING) {
         cudaStream_t user = m->stream, cap = nullptr;
         cudaGraph_t graph = nullptr;
         bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;

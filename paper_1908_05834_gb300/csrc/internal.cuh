@@ -21,7 +21,7 @@ constexpr int kMaxBallsPerCell = 32;
 // Device error word bits (BCHAR_ERR_CAPACITY causes).
 enum : int {
     kErrBallsPerCell = 1,   // a cell has more than kMaxBallsPerCell balls
-    kErrRowCapacity = 2,    // a row has more entries than the slab row capacity
+    kErrRowCapacity = 2,    // (unused: rows wider than the slab go to the spill area)
     kErrWindow = 4,         // a candidate window is larger than the window limit
     kErrSeeds = 8,          // more than kMaxSeeds empty columns
     kErrSeedCapacity = 16,  // a seeded row overflowed the slab row capacity
@@ -76,6 +76,7 @@ struct DevInfo {
     int nonfinite;
     int err;            // capacity error bits
     int need_row_cap;   // largest row length seen
+    int n_spill_rows;   // rows wider than the slab (written to the spill area)
     int void_balls;
     int n_seeds;
     int unbalanced;
@@ -149,13 +150,17 @@ struct bchar_mesh_s {
 
     // per-step buffers
     bchar::Buf t_cell, t_xi, t_rhat;                 // tracked balls
-    bchar::Buf slab_col, slab_val, row_len;          // per-row assembly slab
+    bchar::Buf slab_col, slab_val, row_len;          // per-row assembly slab of row_cap entries per row
+    bchar::Buf spill_cnt, spill_off, spill_col, spill_val;  // rows wider than the slab, at their exact length
     int row_cap = 0;
+    int spill_rows = 0;
     bchar::Buf colcnt, colfill, seeds, seed_row_cnt; // columns, empty-column seeds
     bchar::Buf row_ptr, col_ptr;                     // CSR / CSC pointers
     bchar::Buf col, a0, aN, afin, wgt;               // CSR entries
     bchar::Buf csc_row, csc_src;                     // CSC: row and CSR index of each entry
     bchar::Buf R, C, bloc;                           // scaling factors, balanced row targets
+    bchar::Buf tile_r, tile_c;                       // tiles of the row and column views (first line of each)
+    int64_t ntile = 0;                               // tiles per view
     bchar::Buf uf_parent, uf_label, comp_acc;        // components of A's pattern
     bchar::Buf a2, a2c, diag, qexc, rhs, qx, qy, F, cg_d, cg_r, cg_z, cg_p, cg_q;  // minimisation
     // interior-point state per entry: 1 + x and its upper slack 2 - (1 + x), the bound multipliers,
@@ -210,6 +215,22 @@ inline void launch_dep(void (*kernel)(P...), int grid, int block, cudaStream_t s
     cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
 }
 
+// The same with dynamic shared memory.
+template <typename... P, typename... A>
+inline void launch_dep_smem(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 inline int blocks_for(int64_t n, int threads = kThreads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -229,6 +250,7 @@ void launch_track(bchar_mesh_t m, double dt, int substeps);
 void launch_seed_columns(bchar_mesh_t m, double dt, int substeps);
 // assemble.cu
 void launch_assemble(bchar_mesh_t m);
+bool launch_assemble_spill(bchar_mesh_t m);  // rows wider than the slab, into the spill area (false: no memory)
 void launch_column_counts(bchar_mesh_t m);
 void launch_insert_seeds(bchar_mesh_t m, int nseeds);
 void launch_compact(bchar_mesh_t m);
@@ -238,8 +260,10 @@ VelView vel_view(bchar_mesh_t m);
 // sparse.cu
 void scan_i32_to_i64(bchar_mesh_t m, const int32_t *in, int64_t *out, int64_t n);  // out has n + 1 entries
 void launch_transpose(bchar_mesh_t m);
+bool launch_tiles(bchar_mesh_t m);  // tile boundaries of both views (false: out of memory)
 bool launch_balance(bchar_mesh_t m);  // components.cu
 void launch_scaling(bchar_mesh_t m);
+void launch_scaling_once(bchar_mesh_t m);  // one column and one row scaling (timing aid)
 bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters);  // false: out of memory
 void launch_finalise(bchar_mesh_t m);
 void launch_update(bchar_mesh_t m, const void *c_in, void *c_out, int c_dtype);

@@ -23,6 +23,7 @@
 
 #include "amg.cuh"
 #include "device.cuh"
+#include "tiles.cuh"
 
 namespace bchar {
 
@@ -167,40 +168,171 @@ void launch_transpose(bchar_mesh_t m) {
     m->launches += 2;
 }
 
+// ---------------------------------------------------------------- sub-warp row walks
+//
+// The streaming stages (scalings, update) walk rows of a few to a few tens of
+// entries: L lanes of a warp share one row (L a power of two sized to the mean
+// row length), so consecutive lanes read consecutive entries and a warp reads
+// 32 consecutive entries of neighbouring rows at once.  A row's partial sums
+// are reduced by shuffles within its L lanes.  Every lane of a warp runs the
+// same number of outer iterations (rows past the end contribute nothing), so
+// the shuffles always see the whole warp.  The grid is persistent (a fixed
+// multiple of the SM count), so the order of every sum is fixed.
+
+template <int L> __device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lanes per row for a mean of `mean` entries per row.
+static int lanes_for(double mean) {
+    int L = 2;
+    while (L < 32 && L < mean) L <<= 1;
+    return L;
+}
+
+#define DISPATCH_LANES(L, CALL)                 \
+    switch (L) {                                \
+    case 2: { constexpr int LL = 2; CALL; } break;   \
+    case 4: { constexpr int LL = 4; CALL; } break;   \
+    case 8: { constexpr int LL = 8; CALL; } break;   \
+    case 16: { constexpr int LL = 16; CALL; } break; \
+    default: { constexpr int LL = 32; CALL; } break; \
+    }
+
+constexpr int kStreamBlocks = 152 * 8;  // persistent grid of the streaming kernels (256 threads each)
+
+// ---------------------------------------------------------------- tiles of the two views
+
+template <class K> static void allow_tile_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTileSmem));
+}
+
+__global__ void k_tile_bounds(int64_t n, const int64_t *ptr, int64_t ntile, int32_t *tile) {
+    GRID_STRIDE(k, ntile + 1) {
+        if (k == ntile) {
+            tile[k] = static_cast<int32_t>(n);
+        } else {
+            const int64_t want = k * static_cast<int64_t>(kTileEntries);
+            int64_t lo = 0, hi = n;  // the first l in [0, n] with ptr[l] >= want
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (ptr[mid] >= want) hi = mid;
+                else lo = mid + 1;
+            }
+            tile[k] = static_cast<int32_t>(lo);
+        }
+    }
+}
+
+__global__ void k_scale_tiles(LineView V, const double *f, const double *tgt, double *out);
+__global__ void k_scaled_col_error(LineView V, const double *R, const double *C, const double *volphi,
+                                   unsigned long long *slot);
+__global__ void k_cg_matvec(LineView Vr, LineView Vc, const double *diag, const double *p, double *q,
+                            double *partials, const CgState *st);
+template <class T> __global__ void k_spmv(LineView V, const double *volphi, const T *c_in, T *c_out, double *partials);
+
+bool launch_tiles(bchar_mesh_t m) {
+    static bool attrs = false;  // the shared-memory opt-in of the tile kernels (per process; harmless to repeat)
+    if (!attrs) {
+        allow_tile_smem(k_scale_tiles);
+        allow_tile_smem(k_scaled_col_error);
+        allow_tile_smem(k_cg_matvec);
+        allow_tile_smem(k_spmv<float>);
+        allow_tile_smem(k_spmv<double>);
+        attrs = true;
+    }
+    m->ntile = tile_count(m->nnz);
+    const size_t b = sizeof(int32_t) * (m->ntile + 1);
+    if (!ensure(m, m->tile_r, b) || !ensure(m, m->tile_c, b)) return false;
+    k_tile_bounds<<<blocks_for(m->ntile + 1), kThreads, 0, m->stream>>>(m->nc, ptr<int64_t>(m->row_ptr), m->ntile,
+                                                                        ptr<int32_t>(m->tile_r));
+    k_tile_bounds<<<blocks_for(m->ntile + 1), kThreads, 0, m->stream>>>(m->nc, ptr<int64_t>(m->col_ptr), m->ntile,
+                                                                        ptr<int32_t>(m->tile_c));
+    m->launches += 2;
+    return true;
+}
+
+static LineView row_view(bchar_mesh_t m, const double *val) {
+    return LineView{m->nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), val, ptr<int32_t>(m->tile_r), m->ntile};
+}
+
+static LineView col_view(bchar_mesh_t m, const double *val) {
+    return LineView{m->nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), val, ptr<int32_t>(m->tile_c), m->ntile};
+}
+
+static int tile_grid(int64_t ntiles) { return static_cast<int>(ntiles < kTileBlocks ? (ntiles > 0 ? ntiles : 1) : kTileBlocks); }
+
 // ---------------------------------------------------------------- scaling (eq. volAdj)
 
 __global__ void k_fill(double *v, int64_t n, double val) {
     GRID_STRIDE(i, n) v[i] = val;
 }
 
-// a^{n+1/2}: C_j = |M_j|_phi / sum_i R_i a0_ij
-__global__ void k_colscale(int64_t nc, const int64_t *col_ptr, const int32_t *csc_row, const int32_t *csc_src,
-                           const double *a0, const double *R, const double *volphi, double *C) {
-    GRID_STRIDE(j, nc) {
-        double s = 0.0;
-        for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) s += R[csc_row[p]] * a0[csc_src[p]];
-        C[j] = volphi[j] / s;
+// a0 in column order (a0c[p] = a0[csc_src[p]]), once per step, so that the
+// column passes stream their values.
+__global__ void k_gather_col_values(int64_t nnz, const int32_t *csc_src, const double *a0, double *a0c) {
+    GRID_STRIDE(p, nnz) a0c[p] = a0[csc_src[p]];
+}
+
+// Line sums of one view: out_l = tgt_l / sum_k v_k f[idx_k] over line l (a
+// column of the column view with f = R, or a row of the row view with f = C):
+// a^{n+1/2}: C_j = |M_j|_phi / sum_i R_i a0_ij; a^{n+1}: R_i = b_i / sum_j a0_ij C_j.
+struct ScaleEpi {
+    const double *tgt;
+    double *out;
+    __device__ void operator()(int64_t l, double s) { out[l] = tgt[l] / s; }
+};
+
+struct NoEpi {
+    __device__ void operator()(int64_t, double) {}
+};
+
+__global__ void __launch_bounds__(kTileThreads) k_scale_tiles(LineView V, const double *f, const double *tgt,
+                                                              double *out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ScaleEpi epi{tgt, out};
+    NoEpi none;
+    const LineView nov{0, nullptr, nullptr, nullptr, nullptr, 0};
+    tile_loop(V, f, epi, nov, f, none, smem);
+}
+
+// aN = R a0 C per entry (row view)
+template <int L>
+__global__ void __launch_bounds__(256) k_apply_scaling(int64_t nc, const int64_t *row_ptr, const int32_t *col,
+                                                       const double *a0, const double *R, const double *C,
+                                                       double *aN) {
+    constexpr int G = 256 / L;
+    const int g = threadIdx.x / L, lane = threadIdx.x % L;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * G; base < nc; base += static_cast<int64_t>(gridDim.x) * G) {
+        const int64_t i = base + g;
+        if (i < nc) {
+            const double ri = R[i];
+            for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += L) aN[e] = ri * a0[e] * C[col[e]];
+        }
     }
 }
 
-// a^{n+1}: R_i = b_i / sum_j a0_ij C_j, b_i the (balanced) local target
-__global__ void k_rowscale(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a0,
-                           const double *C, const double *brow, double *R) {
-    GRID_STRIDE(i, nc) {
-        double s = 0.0;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += a0[e] * C[col[e]];
-        R[i] = brow[i] / s;
-    }
+// max_j |C_j sum_i R_i a0_ij - |M_j|_phi| / |M_j|_phi (the column sums of A^(N))
+struct ColErrEpi {
+    const double *C, *volphi;
+    double mx;
+    __device__ void operator()(int64_t j, double s) { mx = fmax(mx, fabs(C[j] * s - volphi[j]) / volphi[j]); }
+};
+
+__global__ void __launch_bounds__(kTileThreads) k_scaled_col_error(LineView V, const double *R, const double *C,
+                                                                   const double *volphi, unsigned long long *slot) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ColErrEpi epi{C, volphi, 0.0};
+    NoEpi none;
+    const LineView nov{0, nullptr, nullptr, nullptr, nullptr, 0};
+    tile_loop(V, R, epi, nov, R, none, smem);
+    const double mx = block_max(epi.mx);
+    if (threadIdx.x == 0) atomic_max_nonneg(slot, mx);
 }
 
-__global__ void k_apply_scaling(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *a0,
-                                const double *R, const double *C, double *aN) {
-    GRID_STRIDE(i, nc) {
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) aN[e] = R[i] * a0[e] * C[col[e]];
-    }
-}
-
-// max_j |sum_i a_ij - |M_j|_phi| / |M_j|_phi
+// max_j |sum_i a_ij - |M_j|_phi| / |M_j|_phi over the column view of a
 __global__ void k_col_error(int64_t nc, const int64_t *col_ptr, const int32_t *csc_src, const double *a,
                             const double *volphi, unsigned long long *slot) {
     double mx = 0.0;
@@ -213,32 +345,47 @@ __global__ void k_col_error(int64_t nc, const int64_t *col_ptr, const int32_t *c
     if (threadIdx.x == 0) atomic_max_nonneg(slot, mx);
 }
 
-void launch_scaling(bchar_mesh_t m) {
-    const int64_t nc = m->nc;
-    const int bl = blocks_for(nc);
-    k_fill<<<bl, kThreads, 0, m->stream>>>(ptr<double>(m->R), nc, 1.0);
+static void scaling_pass(bchar_mesh_t m, bool col_pass, const double *a0c) {
+    const int grid = tile_grid(m->ntile);
+    if (col_pass)
+        k_scale_tiles<<<grid, kTileThreads, kTileSmem, m->stream>>>(col_view(m, a0c), ptr<double>(m->R), ptr<double>(m->volphi),
+                                                            ptr<double>(m->C));
+    else
+        k_scale_tiles<<<grid, kTileThreads, kTileSmem, m->stream>>>(row_view(m, ptr<double>(m->a0)), ptr<double>(m->C),
+                                                            ptr<double>(m->bloc), ptr<double>(m->R));
     ++m->launches;
+}
+
+void launch_scaling(bchar_mesh_t m) {
+    const int64_t nc = m->nc, nnz = m->nnz;
+    const int L = lanes_for(static_cast<double>(nnz) / static_cast<double>(nc > 0 ? nc : 1));
+    double *a0c = ptr<double>(m->a2c);  // scratch until the minimisation: A^(0) in column order
+    k_gather_col_values<<<blocks_for(nnz), kThreads, 0, m->stream>>>(nnz, ptr<int32_t>(m->csc_src), ptr<double>(m->a0),
+                                                                   a0c);
+    k_fill<<<blocks_for(nc), kThreads, 0, m->stream>>>(ptr<double>(m->R), nc, 1.0);
+    m->launches += 2;
     for (int it = 0; it < m->opt.n_scale; ++it) {
-        k_colscale<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
-                                                   ptr<int32_t>(m->csc_src), ptr<double>(m->a0), ptr<double>(m->R),
-                                                   ptr<double>(m->volphi), ptr<double>(m->C));
-        k_rowscale<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                   ptr<double>(m->a0), ptr<double>(m->C), ptr<double>(m->bloc),
-                                                   ptr<double>(m->R));
-        m->launches += 2;
+        scaling_pass(m, true, a0c);
+        scaling_pass(m, false, a0c);
     }
     if (m->opt.n_scale == 0) {
-        k_fill<<<bl, kThreads, 0, m->stream>>>(ptr<double>(m->C), nc, 1.0);
+        k_fill<<<blocks_for(nc), kThreads, 0, m->stream>>>(ptr<double>(m->C), nc, 1.0);
         ++m->launches;
     }
-    k_apply_scaling<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                    ptr<double>(m->a0), ptr<double>(m->R), ptr<double>(m->C),
-                                                    ptr<double>(m->aN));
+    DISPATCH_LANES(L, (k_apply_scaling<LL><<<kStreamBlocks, 256, 0, m->stream>>>(
+                           nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), ptr<double>(m->a0), ptr<double>(m->R),
+                           ptr<double>(m->C), ptr<double>(m->aN))));
     DevInfo *di = ptr<DevInfo>(m->dinfo);
-    k_col_error<<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_src),
-                                                ptr<double>(m->aN), ptr<double>(m->volphi),
-                                                reinterpret_cast<unsigned long long *>(&di->scale_err));
+    k_scaled_col_error<<<tile_grid(m->ntile), kTileThreads, kTileSmem, m->stream>>>(
+        col_view(m, a0c), ptr<double>(m->R), ptr<double>(m->C), ptr<double>(m->volphi),
+        reinterpret_cast<unsigned long long *>(&di->scale_err));
     m->launches += 2;
+}
+
+// One column and one row scaling (timing aid: the streaming stages of a step).
+void launch_scaling_once(bchar_mesh_t m) {
+    scaling_pass(m, true, ptr<double>(m->a2c));
+    scaling_pass(m, false, ptr<double>(m->a2c));
 }
 
 // ---------------------------------------------------------------- minimisation
@@ -307,24 +454,33 @@ __global__ void k_cg_start(const double *partials, int nparts, double target, do
     }
 }
 
-__global__ void k_cg_matvec(int64_t nc, const int64_t *row_ptr, const int32_t *col, const int64_t *col_ptr,
-                            const int32_t *csc_row, const double *a2, const double *a2c, const double *diag,
-                            const double *p, double *q, double *partials, const CgState *st) {
+// q = (A-hat D A-hat^T + diag(exc)) p through the row view (node l < n_c:
+// row l, its entries a2 = a^2 D against the column nodes) and the column view
+// (node n_c + j: column j, its entries a2c against the row nodes), tile by
+// tile (the row view's tiles first), and per-block partial sums of p.q.
+struct MatvecEpi {
+    const double *diag, *p;
+    double *q;
+    int64_t off;  // 0 for the rows, n_c for the columns
+    double acc;
+    __device__ void operator()(int64_t l, double s) {
+        const int64_t node = off + l;
+        const double v = s + diag[node] * p[node];
+        q[node] = v;
+        acc += p[node] * v;
+    }
+};
+
+__global__ void __launch_bounds__(kTileThreads) k_cg_matvec(LineView Vr, LineView Vc, const double *diag,
+                                                            const double *p, double *q, double *partials,
+                                                            const CgState *st) {
     dep_enter();
     if (st->converged) return;
-    double acc = 0.0;
-    GRID_STRIDE(l, 2 * nc) {
-        double s = diag[l] * p[l];
-        if (l < nc) {
-            for (int64_t e = row_ptr[l]; e < row_ptr[l + 1]; ++e) s += a2[e] * p[nc + col[e]];
-        } else {
-            const int64_t j = l - nc;
-            for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k) s += a2c[k] * p[csc_row[k]];
-        }
-        q[l] = s;
-        acc += p[l] * s;
-    }
-    acc = block_sum(acc);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t nc = Vr.n;
+    MatvecEpi er{diag, p, q, 0, 0.0}, ec{diag, p, q, nc, 0.0};
+    tile_loop(Vr, p + nc, er, Vc, p, ec, smem);
+    const double acc = block_sum(er.acc + ec.acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
@@ -860,11 +1016,12 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double ta
     k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
     m->launches += 4;
     const int batch = amg ? 8 : 32;
+    const int mv_grid = tile_grid(2 * m->ntile);  // <= kRedBlocks partial sums of p.q
     auto enqueue_batch = [&]() {
         for (int k = 0; k < batch; ++k) {
-            launch_dep(k_cg_matvec, kRedBlocks, kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                       ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row), a2, a2c, diag, p, q, part, st);
-            launch_dep(k_cg_alpha, 1, 1024, s, part, kRedBlocks, st);
+            launch_dep_smem(k_cg_matvec, mv_grid, kTileThreads, kTileSmem, s, row_view(m, a2), col_view(m, a2c), diag, p,
+                            q, part, st);
+            launch_dep(k_cg_alpha, 1, 1024, s, part, mv_grid, st);
             if (amg) {
                 if (fp32)
                     launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, part_l1,
@@ -1039,8 +1196,12 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
             const int left = m->opt.qp_max_iter - total_cg;
             const int cap = left < kIpCgPerSolve ? left : kIpCgPerSolve;
             // the right-hand side's L1 norm: the node pass's |rp|_1 bounds it well enough for the start
-            total_cg += pcg_solve(m, rhs, hs.rp_l1, target_rz, target_l1, amg, fp32 && amg, cap > 0 ? cap : 1,
-                                  &exec, &graph_launches);
+            const int done = pcg_solve(m, rhs, hs.rp_l1, target_rz, target_l1, amg, fp32 && amg, cap > 0 ? cap : 1,
+                                       &exec, &graph_launches);
+            total_cg += done;
+            if (trace)
+                fprintf(stderr, "[bchar]   solve %d: %d CG iterations, levels %d, coarsest %lld\n", corr, done,
+                        amg ? m->amg.nlev : 0, amg ? static_cast<long long>(m->amg.levels[m->amg.nlev - 1].n) : 0LL);
             launch_dep(k_ip_dir, blr, kThreads, s, nc, row_ptr, col, a, dy, f, u, zl, zh, D, q, cl, ch, df, du, dzl,
                        dzh, part);
             launch_dep(k_ip_dir_nodes, blr, kThreads, s, nc, brow, volphi, gamma, y, dy, p, n, zp, zn, cp, cn, dp, dn,
@@ -1080,11 +1241,9 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
 }
 
 void launch_cg_matvec_once(bchar_mesh_t m, CgState *st) {
-    const int64_t nc = m->nc;
-    k_cg_matvec<<<blocks_for(2 * nc), kThreads, 0, m->stream>>>(
-        nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col), ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
-        ptr<double>(m->a2), ptr<double>(m->a2c), ptr<double>(m->diag), ptr<double>(m->cg_p), ptr<double>(m->cg_q),
-        ptr<double>(m->partials), st);
+    k_cg_matvec<<<tile_grid(2 * m->ntile), kTileThreads, kTileSmem, m->stream>>>(
+        row_view(m, ptr<double>(m->a2)), col_view(m, ptr<double>(m->a2c)), ptr<double>(m->diag), ptr<double>(m->cg_p),
+        ptr<double>(m->cg_q), ptr<double>(m->partials), st);
 }
 
 // ---------------------------------------------------------------- bounds, column fix, W
@@ -1155,13 +1314,16 @@ void launch_finalise(bchar_mesh_t m) {
 
 // ---------------------------------------------------------------- update (eq. phys-inter-ELLAM)
 
-template <class T>
-__global__ void k_spmv(int64_t nc, const int64_t *row_ptr, const int32_t *col, const double *wgt,
-                       const double *volphi, const T *c_in, T *c_out, double *partials) {
-    double mb = 0.0, ma = 0.0, ms = 0.0;
-    GRID_STRIDE(i, nc) {
-        double s = 0.0;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += wgt[e] * static_cast<double>(c_in[col[e]]);
+// c_out_i = sum_j W_ij c_in_j with FP64 accumulation, rounded once on store,
+// tile by tile over the row view, and per-block partial sums of the three
+// masses sum |K|_phi c (before, after the FP64 update, after the stored
+// rounding), all in one pass.
+template <class T> struct SpmvEpi {
+    const double *volphi;
+    const T *c_in;
+    T *c_out;
+    double mb, ma, ms;
+    __device__ void operator()(int64_t i, double s) {
         const T stored = static_cast<T>(s);
         c_out[i] = stored;
         const double v = volphi[i];
@@ -1169,9 +1331,19 @@ __global__ void k_spmv(int64_t nc, const int64_t *row_ptr, const int32_t *col, c
         ma += v * s;
         ms += v * static_cast<double>(stored);
     }
-    mb = block_sum(mb);
-    ma = block_sum(ma);
-    ms = block_sum(ms);
+};
+
+template <class T>
+__global__ void __launch_bounds__(kTileThreads) k_spmv(LineView V, const double *volphi, const T *c_in, T *c_out,
+                                                       double *partials) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SpmvEpi<T> epi{volphi, c_in, c_out, 0.0, 0.0, 0.0};
+    NoEpi none;
+    const LineView nov{0, nullptr, nullptr, nullptr, nullptr, 0};
+    tile_loop(V, c_in, epi, nov, c_in, none, smem);
+    const double mb = block_sum(epi.mb);
+    const double ma = block_sum(epi.ma);
+    const double ms = block_sum(epi.ms);
     if (threadIdx.x == 0) {
         partials[3 * blockIdx.x] = mb;
         partials[3 * blockIdx.x + 1] = ma;
@@ -1197,19 +1369,18 @@ __global__ void k_mass_final(const double *partials, int n, DevInfo *info) {
 }
 
 void launch_update(bchar_mesh_t m, const void *c_in, void *c_out, int c_dtype) {
-    const int64_t nc = m->nc;
-    const int bl = blocks_for(nc);
     double *part = ptr<double>(m->partials);
+    const int grid = tile_grid(m->ntile);
+    static_assert(3 * kTileBlocks <= 4 * 152 * 64, "mass partials fit the scratch");
+    const LineView V = row_view(m, ptr<double>(m->wgt));
     if (c_dtype == BCHAR_C_F32)
-        k_spmv<float><<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                      ptr<double>(m->wgt), ptr<double>(m->volphi),
-                                                      static_cast<const float *>(c_in), static_cast<float *>(c_out), part);
+        k_spmv<float><<<grid, kTileThreads, kTileSmem, m->stream>>>(V, ptr<double>(m->volphi), static_cast<const float *>(c_in),
+                                                            static_cast<float *>(c_out), part);
     else
-        k_spmv<double><<<bl, kThreads, 0, m->stream>>>(nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                       ptr<double>(m->wgt), ptr<double>(m->volphi),
-                                                       static_cast<const double *>(c_in), static_cast<double *>(c_out),
-                                                       part);
-    k_mass_final<<<1, 1024, 0, m->stream>>>(part, bl, ptr<DevInfo>(m->dinfo));
+        k_spmv<double><<<grid, kTileThreads, kTileSmem, m->stream>>>(V, ptr<double>(m->volphi),
+                                                             static_cast<const double *>(c_in),
+                                                             static_cast<double *>(c_out), part);
+    k_mass_final<<<1, 1024, 0, m->stream>>>(part, grid, ptr<DevInfo>(m->dinfo));
     m->launches += 2;
 }
 

@@ -19,6 +19,15 @@
 //     that has collapsed into one node, or an isolated row or column) leaves
 //     the hierarchy: its equation is solved exactly by the smoother (weight 1
 //     instead of kOmega) and it has no coarse counterpart;
+//   - so does a node whose off-diagonal weights sum to at most kDominant of
+//     its diagonal (a constraint held by its shift: in the minimisation's late
+//     iterations, one priced by the linear part of the penalty, or one whose
+//     entries all sit at a bound).  The smoother alone reduces its error by
+//     about that ratio per sweep, and left in, such nodes stall the coarsening
+//     (they have no strong neighbour, so every level keeps them as singletons
+//     and the coarsest level stays large).  Its edges to the nodes that stay
+//     are carried into their coarse shift, so the coarse operator is still the
+//     Galerkin product;
 //   - coarsening stops when a level would keep more than kStall of its
 //     remaining nodes, or has at most kCoarsest of them;
 //   - the coarse operator is the Galerkin product P^T L P for the piecewise-
@@ -54,6 +63,7 @@ constexpr double kStall = 0.9;        // stop coarsening when a level keeps this
 constexpr double kOmega = 0.6;        // Jacobi damping (rows with off-diagonal entries)
 constexpr double kStrength = 0.05;    // strong edge: w_ij >= kStrength sqrt(d_i d_j)
 constexpr double kAttach = 0.25;      // a leftover node follows an edge carrying this share of its diagonal
+constexpr double kDominant = 0.25;    // a node leaves the hierarchy when its off-diagonal sum is this share of its diagonal
 constexpr int kCoarsestSweeps = 40;   // one-block coarsest solve
 constexpr int64_t kFuseBelow = 1 << 19;  // levels smaller than this fuse prolongation with smoothing
 constexpr int kLargeCoarsestSweeps = 20;
@@ -120,21 +130,34 @@ __device__ __forceinline__ bool ranks_above(int64_t i, int32_t j, double w, int3
     return b < 0 || cls > bc || (cls == bc && (hs > bh || (hs == bh && j < b)));
 }
 
+// leave[i] = 1 when node i leaves the hierarchy: no off-diagonal entry, or
+// off-diagonal weights summing to at most kDominant d_i.
+__global__ void k_leaving(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
+                          int32_t *leave) {
+    dep_enter();
+    GRID_STRIDE(i, n) {
+        double w = 0.0;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
+            if (col[e] != i) w -= val[e];
+        leave[i] = (ptr[i + 1] == ptr[i] || w <= kDominant * diag[i]) ? 1 : 0;
+    }
+}
+
 // Top-ranked strong neighbour (off-diagonal weight w_ij = -l_ij > 0 with
-// w_ij >= kStrength sqrt(d_i d_j)); with only_free, among neighbours that are
-// still unpaired.
+// w_ij >= kStrength sqrt(d_i d_j)) among the nodes that stay; with only_free,
+// among neighbours that are still unpaired.
 __global__ void k_heaviest(int64_t n, const int64_t *ptr, const int32_t *col, const double *val, const double *diag,
-                           const int32_t *partner, int only_free, int32_t *best) {
+                           const int32_t *leave, const int32_t *partner, int only_free, int32_t *best) {
     dep_enter();
     GRID_STRIDE(i, n) {
         int32_t b = -1;
         int bc = 0;
         uint32_t bh = 0;
-        if (!only_free || partner[i] < 0) {
+        if (!leave[i] && (!only_free || partner[i] < 0)) {
             const double di = diag[i];
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
                 const int32_t j = col[e];
-                if (j == i) continue;
+                if (j == i || leave[j]) continue;
                 if (only_free && partner[j] >= 0) continue;
                 const double w = -val[e];
                 // strong: w >= kStrength sqrt(d_i d_j), compared squared (no FP64 square root)
@@ -161,22 +184,22 @@ __global__ void k_handshake(int64_t n, const int32_t *best, int32_t *partner) {
     }
 }
 
-// Attachment target of every node: its top-ranked neighbour over all edges
-// when the node's heaviest edge carries at least kAttach of its own diagonal,
-// else -1.  The test is one-sided on purpose: a leaf hanging off a hub by an
-// edge that is strong for the leaf (most of its diagonal) but weak for the
-// hub should follow the hub.
+// Attachment target of every node that stays: its top-ranked neighbour over
+// all edges to nodes that stay when the node's heaviest such edge carries at
+// least kAttach of its own diagonal, else -1.  The test is one-sided on
+// purpose: a leaf hanging off a hub by an edge that is strong for the leaf
+// (most of its diagonal) but weak for the hub should follow the hub.
 __global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
-                                const double *diag, int32_t *att) {
+                                const double *diag, const int32_t *leave, int32_t *att) {
     dep_enter();
     GRID_STRIDE(i, n) {
         int32_t b = -1;
         int bc = 0;
         uint32_t bh = 0;
         double wmax = 0.0;
-        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+        for (int64_t e = leave[i] ? ptr[i + 1] : ptr[i]; e < ptr[i + 1]; ++e) {
             const int32_t j = col[e];
-            if (j == i) continue;
+            if (j == i || leave[j]) continue;
             const double w = -val[e];
             if (!(w > 0.0)) continue;
             wmax = fmax(wmax, w);
@@ -192,16 +215,16 @@ __global__ void k_attach_target(int64_t n, const int64_t *ptr, const int32_t *co
     }
 }
 
-// Leaders, first pass.  A node without off-diagonal entries gets leader -1
+// Leaders, first pass.  A node that leaves the hierarchy gets leader -1
 // (no coarse node; counted in *isolated); a paired node, the smaller node of
 // its pair; an unpaired node whose attachment target is paired joins that
 // pair; every other node is left open (-2) for the second pass.
-__global__ void k_leaders1(int64_t n, const int64_t *ptr, const int32_t *partner, const int32_t *att, int32_t *leader,
-                           int *isolated) {
+__global__ void k_leaders1(int64_t n, const int32_t *leave, const int32_t *partner, const int32_t *att,
+                           int32_t *leader, int *isolated) {
     dep_enter();
     GRID_STRIDE(i, n) {
         int32_t lead = -2;
-        if (ptr[i + 1] == ptr[i]) {
+        if (leave[i]) {
             atomicAdd(isolated, 1);
             lead = -1;
         } else if (partner[i] >= 0) {
@@ -307,7 +330,11 @@ __device__ int coarse_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
         e_sum += exc[m];
         for (int64_t e = ptr[m]; e < ptr[m + 1]; ++e) {
             const int32_t J = agg[col[e]];
-            if (J == I || J < 0) continue;  // internal edge, or a neighbour without coarse counterpart
+            if (J == I) continue;  // internal edge
+            if (J < 0) {           // an edge to a node without coarse counterpart: part of the coarse shift
+                e_sum -= val[e];
+                continue;
+            }
             // insertion into the sorted buffer, merging equal columns
             int pos = cnt;
             while (pos > 0 && cbuf[pos - 1] > J) --pos;
@@ -396,8 +423,13 @@ __device__ int gather_row(int64_t I, const int64_t *mptr, const int32_t *mlist, 
         const int64_t b = ptr[m], e = ptr[m + 1];
         for (int64_t base = b; base < e; base += 32) {
             const int64_t idx = base + lane;
-            const int32_t J = idx < e ? agg[col[idx]] : -1;
-            const bool keep = idx < e && J != I && J >= 0;
+            const int32_t J = idx < e ? agg[col[idx]] : I;
+            const bool keep = J != I && J >= 0;
+            // edges to nodes without coarse counterpart join the shift, added in entry order
+            // (the order of coarse_row)
+            const double shift = J < 0 ? -val[idx] : 0.0;
+            if (__any_sync(0xffffffffu, J < 0))
+                for (int q = 0; q < 32; ++q) e_sum += __shfl_sync(0xffffffffu, shift, q);
             const unsigned mask = __ballot_sync(0xffffffffu, keep);
             const int at = n + __popc(mask & ((1u << lane) - 1u));
             if (keep && at < kMergeCap) {
@@ -873,15 +905,19 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         const int bl = blocks_for(F.n);
         cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * F.n, s);
         cudaMemsetAsync(overflow, 0, 2 * sizeof(int), s);
+        // the want array holds the leave flags until k_want overwrites them
+        launch_dep(k_leaving, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val), fdg,
+                   want);
+        ++m->launches;
         for (int round = 0; round < kHandshakes; ++round) {
             launch_dep(k_heaviest, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val),
-                                               fdg, partner, round > 0, best);
+                                               fdg, want, partner, round > 0, best);
             launch_dep(k_handshake, bl, kThreads, s, F.n, best, partner);
             m->launches += 2;
         }
         launch_dep(k_attach_target, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), ptr<int32_t>(F.col), ptr<double>(F.val), fdg,
-                                                att);
-        launch_dep(k_leaders1, bl, kThreads, s, F.n, ptr<int64_t>(F.ptr), partner, att, leader, isolated);
+                                                want, att);
+        launch_dep(k_leaders1, bl, kThreads, s, F.n, want, partner, att, leader, isolated);
         launch_dep(k_want, bl, kThreads, s, F.n, att, leader, want);
         launch_dep(k_leaders2, bl, kThreads, s, F.n, want, leader, flag);
         m->launches += 4;

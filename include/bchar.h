@@ -209,15 +209,18 @@ enum {
     BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
     BCHAR_STAGE_TRACK = 3,     /* RK4 tracking of all balls */
     BCHAR_STAGE_SMOOTH = 4,    /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
-    BCHAR_STAGE_SCALING = 5    /* one column and one row scaling of eq. volAdj (on scratch copies) */
+    BCHAR_STAGE_SCALING = 5,   /* one column and one row scaling of eq. volAdj (on scratch copies) */
+    BCHAR_STAGE_VCYCLE = 6     /* one FP32 V-cycle of the multigrid preconditioner (the last one built) */
 };
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of
  * the last step, on the handle's stream, and return the mean duration of one
- * launch in milliseconds (CUDA events around the replays).  CG_MATVEC, UPDATE
- * and SMOOTH are replayed from one CUDA graph of `reps` launches (captured on a
- * private stream), so that host launch overhead is not measured; SCALING too
- * (it writes the scaling factors, which the step no longer needs).  The replays do
+ * launch in milliseconds (CUDA events around the replays).  CG_MATVEC, UPDATE,
+ * SMOOTH and VCYCLE are replayed from one CUDA graph of `reps` launches
+ * (captured on a private stream), so that host launch overhead is not
+ * measured; SCALING too (it writes the scaling factors, which the step no
+ * longer needs).  VCYCLE (a chain of kernels, one per pass and level) needs a
+ * step that built the multigrid hierarchy, like SMOOTH.  The replays do
  * not change the result of the last step (exports stay valid) except that
  * BCHAR_STAGE_TRACK overwrites the tracked balls with the same values.
  * Errors: INVALID_ARG (no step yet, bad stage, reps < 1), CUDA. */

@@ -92,7 +92,7 @@ lib.bchar_export_tracked.restype = ctypes.c_int
 lib.bchar_time_stage.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
 lib.bchar_time_stage.restype = ctypes.c_int
 
-STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK, STAGE_SMOOTH, STAGE_SCALING = 0, 1, 2, 3, 4, 5
+STAGE_CG_MATVEC, STAGE_UPDATE, STAGE_ASSEMBLE, STAGE_TRACK, STAGE_SMOOTH, STAGE_SCALING, STAGE_VCYCLE = range(7)
 
 lib.bchar_mass_noalloc.argtypes = [_P, _P, ctypes.c_int, _I64, _P, _P]
 lib.bchar_mass_noalloc.restype = ctypes.c_int

@@ -56,7 +56,7 @@ namespace bchar {
 
 constexpr int kCoarseCap = 384;       // neighbours a coarse node may collect before merging
 constexpr int64_t kCoarsest = 128;    // stop coarsening at this many nodes
-constexpr int64_t kOneBlock = 4096;   // coarsest levels up to this size are swept by one block
+constexpr int64_t kOneBlock = 4096;   // levels up to this size are cycled by one block
 constexpr int kMaxLevels = 40;
 constexpr int kHandshakes = 4;        // matching rounds per level
 constexpr double kStall = 0.9;        // stop coarsening when a level keeps this fraction of nodes
@@ -64,9 +64,10 @@ constexpr double kOmega = 0.6;        // Jacobi damping (rows with off-diagonal 
 constexpr double kStrength = 0.05;    // strong edge: w_ij >= kStrength sqrt(d_i d_j)
 constexpr double kAttach = 0.25;      // a leftover node follows an edge carrying this share of its diagonal
 constexpr double kDominant = 0.25;    // a node leaves the hierarchy when its off-diagonal sum is this share of its diagonal
-constexpr int kCoarsestSweeps = 40;   // one-block coarsest solve
+constexpr int kCoarsestSweeps = 40;   // sweeps of a one-block coarsest level
 constexpr int64_t kFuseBelow = 1 << 19;  // levels smaller than this fuse prolongation with smoothing
 constexpr int kLargeCoarsestSweeps = 20;
+constexpr int kDominantSweeps = 4;
 
 // ---------------------------------------------------------------- level 0
 
@@ -773,22 +774,83 @@ template <class T> __global__ void k_prolong(int64_t n, const int32_t *agg, cons
     }
 }
 
-// Coarsest level: kCoarsestSweeps damped-Jacobi sweeps from zero, all in one
-// block (the level is small), double-buffered in global memory.
+// The levels small enough for one block (n <= kOneBlock each), from the
+// first of them down to the coarsest and back, in one launch: the same
+// arithmetic per node as the per-level kernels above (pre-smoothing fused with
+// the residual, restriction, kCoarsestSweeps sweeps on the coarsest level,
+// prolongation fused with post-smoothing), with a block barrier between the
+// passes instead of a kernel boundary.  On a fine mesh the hierarchy has a
+// handful of such levels, each of which otherwise costs three launches of a
+// few microseconds that do almost no work.
+template <class T> struct SmallLevel {
+    int64_t n;
+    const int64_t *ptr;
+    const int32_t *col;
+    const T *val, *diag;
+    const int32_t *agg;    // node -> aggregate of the next level (levels above the coarsest)
+    const int64_t *mptr;   // members (nodes of the previous level) of each node of this level
+    const int32_t *mlist;
+    T *x, *x2, *b, *r;
+};
+
 template <class T>
-__global__ void k_coarsest(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *b,
-                           T *x, T *x2, const CgState *st) {
+__global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, int nl, const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
-    __syncthreads();
-    for (int k = 0; k < kCoarsestSweeps; ++k) {
-        const T *xi = (k & 1) ? x2 : x;
-        T *xo = (k & 1) ? x : x2;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            T s = diag[i] * xi[i];
-            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * xi[col[e]];
-            xo[i] = xi[i] + static_cast<T>(row_weight(ptr, i)) * (b[i] - s) / diag[i];
+    const T om = static_cast<T>(kOmega);
+    for (int l = 0; l + 1 < nl; ++l) {  // down
+        const SmallLevel<T> &L = Ls[l];
+        for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x) {
+            const int64_t e0 = L.ptr[i], e1 = L.ptr[i + 1];
+            const T bi = L.b[i], di = L.diag[i];
+            const T xi = static_cast<T>(e1 == e0 ? 1.0 : kOmega) * bi / di;
+            L.x[i] = xi;
+            T sum = di * xi;
+            for (int64_t e = e0; e < e1; ++e) {
+                const int32_t j = L.col[e];
+                sum += L.val[e] * (om * L.b[j] / L.diag[j]);
+            }
+            L.r[i] = bi - sum;
+        }
+        __syncthreads();
+        const SmallLevel<T> &C = Ls[l + 1];
+        for (int64_t I = threadIdx.x; I < C.n; I += blockDim.x) {
+            T sum = 0;
+            for (int64_t k = C.mptr[I]; k < C.mptr[I + 1]; ++k) sum += L.r[C.mlist[k]];
+            C.b[I] = sum;
+        }
+        __syncthreads();
+    }
+    {  // coarsest
+        const SmallLevel<T> &L = Ls[nl - 1];
+        for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x)
+            L.x[i] = static_cast<T>(row_weight(L.ptr, i)) * L.b[i] / L.diag[i];
+        __syncthreads();
+        for (int k = 0; k < kCoarsestSweeps; ++k) {
+            const T *xi = (k & 1) ? L.x2 : L.x;
+            T *xo = (k & 1) ? L.x : L.x2;
+            for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x) {
+                T sum = L.diag[i] * xi[i];
+                for (int64_t e = L.ptr[i]; e < L.ptr[i + 1]; ++e) sum += L.val[e] * xi[L.col[e]];
+                xo[i] = xi[i] + static_cast<T>(row_weight(L.ptr, i)) * (L.b[i] - sum) / L.diag[i];
+            }
+            __syncthreads();
+        }
+    }
+    for (int l = nl - 2; l >= 0; --l) {  // up
+        const SmallLevel<T> &L = Ls[l];
+        const T *xc = l + 1 == nl - 1 ? Ls[l + 1].x : Ls[l + 1].x2;
+        for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x) {
+            const int64_t e0 = L.ptr[i], e1 = L.ptr[i + 1];
+            const int32_t I = L.agg[i];
+            const T xi = I >= 0 ? L.x[i] + xc[I] : L.x[i];
+            T sum = L.diag[i] * xi;
+            for (int64_t e = e0; e < e1; ++e) {
+                const int32_t j = L.col[e];
+                const int32_t J = L.agg[j];
+                sum += L.val[e] * (J >= 0 ? L.x[j] + xc[J] : L.x[j]);
+            }
+            L.x2[i] = xi + static_cast<T>(e1 == e0 ? 1.0 : kOmega) * (L.b[i] - sum) / L.diag[i];
         }
         __syncthreads();
     }
@@ -804,6 +866,8 @@ void amg_release(Amg &amg) {
     }
     amg.levels.clear();
     release(amg.tmp);
+    release(amg.small_f);
+    release(amg.small_d);
 }
 
 static bool level_vectors(bchar_mesh_t m, AmgLevel &L) {
@@ -849,6 +913,39 @@ static bool amg_reoperate(bchar_mesh_t m, Amg &amg, bool &overflowed) {
 
 static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg);
 
+// The one-block levels: every level from the first with at most kOneBlock
+// nodes down to the coarsest (levels shrink, so they are a suffix), when the
+// coarsest is one of them.  Their descriptors go to the device once per build.
+static bool small_descriptors(bchar_mesh_t m, Amg &amg) {
+    int from = amg.nlev;
+    while (from > 0 && amg.levels[from - 1].n <= kOneBlock) --from;
+    amg.small_from = from;
+    const int nl = amg.nlev - from;
+    if (nl == 0) return true;
+    std::vector<SmallLevel<float>> hf(nl);
+    std::vector<SmallLevel<double>> hd(nl);
+    for (int k = 0; k < nl; ++k) {
+        AmgLevel &L = amg.levels[from + k];
+        const bool last = from + k == amg.nlev - 1;
+        const bool first = k == 0;
+        hf[k] = {L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<float>(L.fval), ptr<float>(L.fdiag),
+                 last ? nullptr : ptr<int32_t>(L.agg), first ? nullptr : ptr<int64_t>(L.mptr),
+                 first ? nullptr : ptr<int32_t>(L.mlist), ptr<float>(L.fx), ptr<float>(L.fx2), ptr<float>(L.fb),
+                 ptr<float>(L.fr)};
+        hd[k] = {L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.dval), ptr<double>(L.ddiag),
+                 last ? nullptr : ptr<int32_t>(L.agg), first ? nullptr : ptr<int64_t>(L.mptr),
+                 first ? nullptr : ptr<int32_t>(L.mlist), ptr<double>(L.x), ptr<double>(L.x2), ptr<double>(L.b),
+                 ptr<double>(L.r)};
+    }
+    if (!ensure(m, amg.small_f, sizeof(SmallLevel<float>) * nl) ||
+        !ensure(m, amg.small_d, sizeof(SmallLevel<double>) * nl))
+        return false;
+    // pageable sources: the copies have read them when the calls return
+    cudaMemcpyAsync(amg.small_f.p, hf.data(), sizeof(SmallLevel<float>) * nl, cudaMemcpyHostToDevice, m->stream);
+    cudaMemcpyAsync(amg.small_d.p, hd.data(), sizeof(SmallLevel<double>) * nl, cudaMemcpyHostToDevice, m->stream);
+    return true;
+}
+
 bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
     cudaStream_t s = m->stream;
     const int64_t nc = m->nc, nnz = m->nnz;
@@ -871,6 +968,7 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         // a coarse row of the kept hierarchy overflows on this matrix: build anew
     }
     amg.nlev = 1;
+    amg.large_sweeps = kLargeCoarsestSweeps;
     AmgLevel &L0 = amg.levels[0];
     L0.n = 2 * nc;
     L0.nnz = 2 * nnz;
@@ -961,6 +1059,9 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return false;
         m->launches += 1;
         const int64_t active = Fr.n - niso;  // nodes that would have a coarse counterpart
+        // a coarsest level whose nodes have all left the hierarchy is diagonally
+        // dominant (ratio <= kDominant): a few sweeps reduce its error enough
+        amg.large_sweeps = active == 0 ? kDominantSweeps : kLargeCoarsestSweeps;
         if (active <= kCoarsest || nco >= active * kStall || nco < 1) break;  // Fr is the coarsest level
         if (ovf) break;  // a coarse row would be too wide: stop at the finer level
         C.n = nco;
@@ -998,7 +1099,7 @@ static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg) {
         launch_dep(k_scaled_copy<double>, blocks_for(L.n), kThreads, s, L.n, dg, ptr<double>(L.ddiag), inv);
         m->launches += 4;
     }
-    return true;
+    return small_descriptors(m, amg);
 }
 
 // Buffers of one level in the V-cycle's precision.
@@ -1010,6 +1111,7 @@ template <> struct LevelBufs<float> {
     static float *x2(AmgLevel &L) { return ptr<float>(L.fx2); }
     static float *b(AmgLevel &L) { return ptr<float>(L.fb); }
     static float *r(AmgLevel &L) { return ptr<float>(L.fr); }
+    static void *small(Amg &a) { return a.small_f.p; }
 };
 template <> struct LevelBufs<double> {
     static double *val(AmgLevel &L) { return ptr<double>(L.dval); }
@@ -1018,6 +1120,7 @@ template <> struct LevelBufs<double> {
     static double *x2(AmgLevel &L) { return ptr<double>(L.x2); }
     static double *b(AmgLevel &L) { return ptr<double>(L.b); }
     static double *r(AmgLevel &L) { return ptr<double>(L.r); }
+    static void *small(Amg &a) { return a.small_d.p; }
 };
 
 // z = S V(S res) / scale: one V-cycle of the sign-flipped operator in precision T.
@@ -1032,7 +1135,8 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
         launch_dep(k_flip_in<T>, blocks_for(L0.n), kThreads, s, nc, res, B::b(L0), st);
         ++m->launches;
     }
-    for (int l = 0; l < amg.nlev - 1; ++l) {  // down: pre-smooth from zero, residual, restrict
+    const int big = amg.small_from < amg.nlev ? amg.small_from : amg.nlev - 1;  // levels cycled kernel by kernel
+    for (int l = 0; l < big; ++l) {  // down: pre-smooth from zero, residual, restrict
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
@@ -1042,24 +1146,23 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
                                                            B::b(C), st);
         m->launches += 2;
     }
-    {  // coarsest: Jacobi sweeps from zero (an even number, so the result is in x)
+    if (amg.small_from < amg.nlev) {  // the one-block levels down to the coarsest and back, one launch
+        launch_dep(k_small_cycle<T>, 1, 1024, s, static_cast<const SmallLevel<T> *>(B::small(amg)),
+                                             amg.nlev - amg.small_from, st);
+        ++m->launches;
+    } else {  // a coarsest level too large for one block: Jacobi sweeps from zero (even count: the result is in x)
         AmgLevel &L = amg.levels[amg.nlev - 1];
-        if (L.n <= kOneBlock) {
-            launch_dep(k_coarsest<T>, 1, 1024, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L), B::diag(L),
-                                             B::b(L), B::x(L), B::x2(L), st);
-            ++m->launches;
-        } else {
-            const int bl = blocks_for(L.n);
-            launch_dep(k_jacobi0<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
-            for (int k = 0; k < kLargeCoarsestSweeps; ++k)
-                launch_dep(k_jacobi<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
-                                                    B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
-                                                    k & 1 ? B::x(L) : B::x2(L), st);
-            m->launches += 1 + kLargeCoarsestSweeps;
-        }
+        const int bl = blocks_for(L.n);
+        launch_dep(k_jacobi0<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
+        for (int k = 0; k < amg.large_sweeps; ++k)
+            launch_dep(k_jacobi<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
+                                                B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
+                                                k & 1 ? B::x(L) : B::x2(L), st);
+        m->launches += 1 + amg.large_sweeps;
     }
-    // up: prolong into x, post-smooth into x2 (the next finer level reads x2)
-    for (int l = amg.nlev - 2; l >= 0; --l) {
+    // up: prolong into x, post-smooth into x2 (the next finer level reads x2; the
+    // coarsest level, and a one-block cycle of a single level, leave theirs in x)
+    for (int l = big - 1; l >= 0; --l) {
         AmgLevel &L = amg.levels[l];
         AmgLevel &C = amg.levels[l + 1];
         const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);

@@ -597,8 +597,8 @@ bchar_status bchar_estimate_device_bytes(int dim, const int64_t *n_cells, const 
 
 bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_ms) {
     if (!m) return BCHAR_ERR_INVALID_ARG;
-    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 5 ||
-        (stage == BCHAR_STAGE_SMOOTH && m->amg_levels == 0))
+    if (!m->have_step || reps < 1 || !mean_ms || stage < 0 || stage > 6 ||
+        ((stage == BCHAR_STAGE_SMOOTH || stage == BCHAR_STAGE_VCYCLE) && m->amg_levels == 0))
         return fail(m, BCHAR_ERR_INVALID_ARG, "no step yet or bad arguments");
     Buf st, cin, cout;
     if (!ensure(m, st, sizeof(CgState)) || !ensure(m, cin, sizeof(double) * m->nc) ||
@@ -617,6 +617,9 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
         case BCHAR_STAGE_UPDATE: launch_update(m, cin.p, cout.p, BCHAR_C_F64); break;
         case BCHAR_STAGE_ASSEMBLE: launch_assemble(m); break;
         case BCHAR_STAGE_SMOOTH: amg_smooth_once(m, m->amg); break;
+        case BCHAR_STAGE_VCYCLE:  // on the finest right-hand side left by the last solve; z is scratch after the step
+            amg_apply(m, m->amg, nullptr, ptr<double>(m->cg_z), nullptr, true, true);
+            break;
         case BCHAR_STAGE_SCALING: launch_scaling_once(m); break;
         default: launch_track(m, m->dt, m->substeps); break;
         }
@@ -627,7 +630,7 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
     // graph is captured on a private stream and launched on the handle's.
     cudaGraphExec_t exec = nullptr;
     if (stage == BCHAR_STAGE_CG_MATVEC || stage == BCHAR_STAGE_UPDATE || stage == BCHAR_STAGE_SMOOTH ||
-        stage == BCHAR_STAGE_SCALING) {
+        stage == BCHAR_STAGE_SCALING || stage == BCHAR_STAGE_VCYCLE) {
         cudaStream_t user = m->stream, cap = nullptr;
         cudaGraph_t graph = nullptr;
         bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;

@@ -85,8 +85,8 @@ struct DevInfo {
 
 // Conjugate-gradient scalars.
 struct CgState {
-    double rz, rz_new, pq, alpha, beta, res_l1, target;
-    double target_l1;  // the solve also needs |res|_1 <= target_l1
+    double rz, rz_new, pq, alpha, beta, res_max, target;
+    double target_res;  // the solve also needs max_l |res_l| / b_l <= target_res (b_l: the constraint's target)
     int converged;
     int iters;
 };
@@ -116,6 +116,9 @@ struct Amg {
     int nlev = 0;
     Buf tmp;
     double scale = 1.0;  // the FP32 levels hold operator / scale
+    int small_from = 0;        // levels small_from..nlev-1 are cycled by one block (nlev: none)
+    int large_sweeps = 0;      // Jacobi sweeps of a coarsest level too large for one block
+    Buf small_f, small_d;      // device descriptors of the small levels (FP32 / FP64 operators)
 };
 
 }  // namespace bchar

@@ -437,9 +437,16 @@ __global__ void k_dot(int64_t n, const double *a, const double *b, double *parti
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// The target b_l of constraint node l: |K_l|_phi-balanced row target for a
+// row node, |M_j|_phi for a column node.
+__device__ __forceinline__ double ip_target(int64_t nc, int64_t l, const double *b_row, const double *volphi) {
+    return l < nc ? b_row[l] : volphi[l - nc];
+}
+
 // Start of a solve: z.res of the initial residual, the two stopping targets
-// (z.res <= target and |res|_1 <= target_l1; the initial |res|_1 is rhs_l1).
-__global__ void k_cg_start(const double *partials, int nparts, double target, double target_l1, double rhs_l1,
+// (z.res <= target and max_l |res_l| / b_l <= target_res; the initial value of
+// the latter is rhs_max).
+__global__ void k_cg_start(const double *partials, int nparts, double target, double target_res, double rhs_max,
                            CgState *st) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partials[i];
@@ -447,9 +454,9 @@ __global__ void k_cg_start(const double *partials, int nparts, double target, do
     if (threadIdx.x == 0) {
         st->rz = s;
         st->target = target;
-        st->target_l1 = target_l1;
-        st->res_l1 = rhs_l1;
-        st->converged = (s == 0.0) || (s <= target && rhs_l1 <= target_l1);
+        st->target_res = target_res;
+        st->res_max = rhs_max;
+        st->converged = (s == 0.0) || (s <= target && rhs_max <= target_res);
         st->iters = 0;
     }
 }
@@ -496,24 +503,25 @@ __global__ void k_cg_alpha(const double *partials, int nparts, CgState *st) {
     }
 }
 
-// d += alpha p, res -= alpha q (the previous residual kept in rp), partial
-// sums of |res|
+// d += alpha p, res -= alpha q (the previous residual kept in rp), per-block
+// maxima of |res_l| / b_l (res is the constraint residual the direction leaves)
 __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double *d, double *res, double *rp,
-                            double *partials, const CgState *st) {
+                            const double *b_row, const double *volphi, double *partials, const CgState *st) {
     dep_enter();
     if (st->converged) return;
     const double alpha = st->alpha;
-    double l1 = 0.0;
+    const int64_t nc = n2 / 2;
+    double mx = 0.0;
     GRID_STRIDE(l, n2) {
         d[l] += alpha * p[l];
         const double r0 = res[l];
         rp[l] = r0;
         const double r = r0 - alpha * q[l];
         res[l] = r;
-        l1 += fabs(r);
+        mx = fmax(mx, fabs(r) / ip_target(nc, l, b_row, volphi));
     }
-    l1 = block_sum(l1);
-    if (threadIdx.x == 0) partials[blockIdx.x] = l1;
+    mx = block_max(mx);
+    if (threadIdx.x == 0) partials[blockIdx.x] = mx;
 }
 
 // The same, also writing the next V-cycle's right-hand side b = S res in its
@@ -521,11 +529,11 @@ __global__ void k_cg_update(int64_t n2, const double *p, const double *q, double
 // its own over res.
 template <class T>
 __global__ void k_cg_update_b(int64_t nc, const double *p, const double *q, double *d, double *res, double *rp,
-                              double *partials, T *b, const CgState *st) {
+                              const double *b_row, const double *volphi, double *partials, T *b, const CgState *st) {
     dep_enter();
     if (st->converged) return;
     const double alpha = st->alpha;
-    double l1 = 0.0;
+    double mx = 0.0;
     GRID_STRIDE(l, 2 * nc) {
         d[l] += alpha * p[l];
         const double r0 = res[l];
@@ -533,10 +541,10 @@ __global__ void k_cg_update_b(int64_t nc, const double *p, const double *q, doub
         const double r = r0 - alpha * q[l];
         res[l] = r;
         b[l] = static_cast<T>(l < nc ? r : -r);
-        l1 += fabs(r);
+        mx = fmax(mx, fabs(r) / ip_target(nc, l, b_row, volphi));
     }
-    l1 = block_sum(l1);
-    if (threadIdx.x == 0) partials[blockIdx.x] = l1;
+    mx = block_max(mx);
+    if (threadIdx.x == 0) partials[blockIdx.x] = mx;
 }
 
 // partial sums of z.res and z.rp (flexible, Polak-Ribiere form of beta: the
@@ -558,25 +566,25 @@ __global__ void k_dot2(int64_t n, const double *z, const double *res, const doub
     }
 }
 
-__global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const double *l1_parts, int nparts,
+__global__ void k_cg_beta(const double *rz_parts, const double *zp_parts, const double *res_parts, int nparts,
                           CgState *st) {
     dep_enter();
     if (st->converged) return;
-    double rz = 0.0, zp = 0.0, l1 = 0.0;
+    double rz = 0.0, zp = 0.0, mx = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
         rz += rz_parts[i];
         zp += zp_parts[i];
-        l1 += l1_parts[i];
+        mx = fmax(mx, res_parts[i]);
     }
     rz = block_sum(rz);
     zp = block_sum(zp);
-    l1 = block_sum(l1);
+    mx = block_max(mx);
     if (threadIdx.x == 0) {
         st->beta = st->rz > 0.0 ? fmax(0.0, (rz - zp) / st->rz) : 0.0;
         st->rz = rz;
-        st->res_l1 = l1;
+        st->res_max = mx;
         st->iters += 1;
-        if ((rz <= st->target && l1 <= st->target_l1) || !(st->pq > 0.0) || !(rz > 0.0)) st->converged = 1;
+        if ((rz <= st->target && mx <= st->target_res) || !(st->pq > 0.0) || !(rz > 0.0)) st->converged = 1;
     }
 }
 
@@ -643,10 +651,6 @@ __device__ __forceinline__ double ip_node_sum(int64_t nc, int64_t l, const int64
         }
     }
     return s;
-}
-
-__device__ __forceinline__ double ip_target(int64_t nc, int64_t l, const double *b_row, const double *volphi) {
-    return l < nc ? b_row[l] : volphi[l - nc];
 }
 
 // Node pass: constraint residual rp_l = b_l - (A-hat f)_l - eps^2 b_l^2 y_l - b_l (p_l - n_l),
@@ -989,12 +993,12 @@ constexpr int kStallIters = 400;
 // squared error of d in the norm of the matrix, which bounds the error of
 // A-hat^T d where the interior-point direction needs it -- an L1 test alone
 // would not bound the error along the nearly singular modes of weakly linked
-// cells) and |res|_1 <= target_l1 (the residual feeds the next constraint
-// residual).  One batch of iterations is captured into a CUDA graph
+// cells) and max_l |res_l| / b_l <= target_res (after a full step, res is the
+// constraint residual, which the interior point measures in that norm).  One batch of iterations is captured into a CUDA graph
 // per preconditioner build (*exec; destroyed by the caller) and replayed until
 // the solve has converged (its kernels do nothing then); the host polls once
 // per batch.  Returns the iterations done.
-static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double target_rz, double target_l1, bool amg,
+static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double target_res, bool amg,
                      bool fp32, int max_iter, cudaGraphExec_t *exec, int *graph_launches) {
     const int64_t nc = m->nc, n2 = 2 * nc;
     const int bl = blocks_for(n2);
@@ -1003,7 +1007,8 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double ta
     double *d = ptr<double>(m->cg_d), *res = ptr<double>(m->cg_r), *z = ptr<double>(m->cg_z);
     double *p = ptr<double>(m->cg_p), *q = ptr<double>(m->cg_q), *rp = ptr<double>(m->cg_rp);
     double *part = ptr<double>(m->partials);
-    double *part_l1 = part + 152 * 64;
+    double *part_res = part + 152 * 64;
+    const double *brow = ptr<double>(m->bloc), *volphi = ptr<double>(m->volphi);
     double *part_rz = part + 2 * 152 * 64;
     double *part_zp = part + 3 * 152 * 64;
     CgState *st = ptr<CgState>(m->cg);
@@ -1012,7 +1017,8 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double ta
     k_copy<<<bl, kThreads, 0, s>>>(n2, rhs, res, nullptr);
     precondition(m, amg, fp32, res, z, nullptr);
     k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
-    k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, target_rz, target_l1, rhs_l1, st);
+    // the right-hand side's residual norm is not formed: the first iteration checks it
+    k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, target_rz, target_res, INFINITY, st);
     k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
     m->launches += 4;
     const int batch = amg ? 8 : 32;
@@ -1024,20 +1030,20 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double ta
             launch_dep(k_cg_alpha, 1, 1024, s, part, mv_grid, st);
             if (amg) {
                 if (fp32)
-                    launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, part_l1,
+                    launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, brow, volphi, part_res,
                                static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
                 else
-                    launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, part_l1,
+                    launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, brow, volphi, part_res,
                                static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
                 precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
                 m->launches += 3;
             } else {
-                launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, part_l1, st);
+                launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, brow, volphi, part_res, st);
                 precondition(m, amg, fp32, res, z, st);
                 launch_dep(k_dot2, kRedBlocks, kThreads, s, n2, z, res, rp, part_rz, part_zp, st);
                 m->launches += 4;
             }
-            launch_dep(k_cg_beta, 1, 1024, s, part_rz, part_zp, part_l1, kRedBlocks, st);
+            launch_dep(k_cg_beta, 1, 1024, s, part_rz, part_zp, part_res, kRedBlocks, st);
             launch_dep(k_cg_pupdate, bl, kThreads, s, n2, z, p, st);
             m->launches += 2;
         }
@@ -1071,8 +1077,8 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double rhs_l1, double ta
         cudaMemcpyAsync(host_st, st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         if (host_st->converged || host_st->iters >= max_iter) break;
-        if (host_st->res_l1 < 0.99 * best) {
-            best = host_st->res_l1;
+        if (host_st->res_max < 0.99 * best) {
+            best = host_st->res_max;
             best_at = host_st->iters;
         } else if (host_st->iters - best_at >= kStallIters) {
             break;
@@ -1097,6 +1103,12 @@ constexpr double kLinearFrom = 1e-6;
 // (y and the multipliers reach ~gamma where the problem is infeasible, and the
 // residuals then carry that much rounding).
 constexpr double kIpMuTol = 1e-12;
+// The corrector's centring target never goes below kIpMuFloor: once the mean
+// complementarity meets its tolerance, the iterations that are still needed to
+// bring the constraint residual down hold it there instead of driving it
+// towards zero (which makes the normal equations so badly conditioned that the
+// inexact solves raise the constraint residual again).
+constexpr double kIpMuFloor = 0.1 * kIpMuTol;
 // Conjugate-gradient iterations per interior-point solve at most (the late
 // normal equations are badly conditioned; an inexact direction is corrected by
 // the next iteration).
@@ -1178,16 +1190,16 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
         m->launches += 2;
         const bool amg = use_amg && amg_build(m, m->amg, false);
         // each direction solved until its squared energy-norm error is about <= 1e-2 mu (then
-        // every entry's step error stays about <= 0.1 of its distance to the bound) and its
-        // residual is <= 0.1 of the constraint residual (which the step then reduces), but
-        // not below the rounding of the solve, 1e-12 of sum |K|_phi
+        // every entry's step error stays about <= 0.1 of its distance to the bound) and the
+        // constraint residual it leaves is, relative to each target, <= 0.1 of the current
+        // one (which the step then reduces), but not below half the stopping tolerance
         const double target_rz = 1e-2 * mu;
-        const double target_l1 = fmax(0.1 * hs.rp_l1, 1e-12 * m->sum_volphi);
+        const double target_res = fmax(0.1 * hs.rp_max, 0.5 * m->opt.qp_tol);
         const bool fp32 = mu > 1e-6;
         cudaGraphExec_t exec = nullptr;
         int graph_launches = 0;
         for (int corr = 0; corr < 2; ++corr) {
-            const double sigma_mu = corr ? fmin(1.0, pow(hs.comp_aff / hs.comp, 3.0)) * mu : 0.0;
+            const double sigma_mu = corr ? fmax(fmin(1.0, pow(hs.comp_aff / hs.comp, 3.0)) * mu, kIpMuFloor) : 0.0;
             launch_dep(k_ip_q, blr, kThreads, s, nc, row_ptr, col, a, y, f, u, zl, zh, corr, sigma_mu, df, du, dzl,
                        dzh, cl, ch, q);
             launch_dep(k_ip_rhs, bl2, kThreads, s, nc, row_ptr, col_ptr, csc_src, a, D, q, rp, brow, volphi, gamma, y,
@@ -1196,7 +1208,7 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
             const int left = m->opt.qp_max_iter - total_cg;
             const int cap = left < kIpCgPerSolve ? left : kIpCgPerSolve;
             // the right-hand side's L1 norm: the node pass's |rp|_1 bounds it well enough for the start
-            const int done = pcg_solve(m, rhs, hs.rp_l1, target_rz, target_l1, amg, fp32 && amg, cap > 0 ? cap : 1,
+            const int done = pcg_solve(m, rhs, target_rz, target_res, amg, fp32 && amg, cap > 0 ? cap : 1,
                                        &exec, &graph_launches);
             total_cg += done;
             if (trace)

@@ -1,22 +1,31 @@
-"""Benchmark: B-char cell-steps/s on the 1024x1024 single-vortex workload.
+"""Benchmark: B-char cell-steps/s of whole time steps on one GB300.
 
-One "step" is one time step of the whole hot path on one GPU: setting the
-step's velocity (with its checks) and bchar_step (tracking, intersections,
-scalings, minimisation, weights, update), through the C ABI.
+One step is one time step of the whole hot path through the C ABI: setting the
+step's velocity (with its checks) and bchar_step -- RK4 tracking of the balls,
+ball intersections and row assembly, column balancing, the N = 10 alternating
+scalings, the bounded mass-conservation minimisation solved to the library's
+default tolerance, the final weights and the update c <- W c.  The default
+workload is the 1024 x 1024 stretched-mesh single vortex (FP32 tracking and
+intersections, FP64 sums and minimisation), the largest configuration whose
+steps finish in seconds; --workload picks another recipe.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank runs its own replica of the workload on its
-own GPU (the method is single-GPU; replicas only) and rank 0 prints one JSON
+own GPU (the method does not shard: replicas only) and rank 0 prints one JSON
 line with the whole-job rate.  --impl reference times the FP64 CPU oracle on
-the host cores on a bounded sample of the same workload.
+all host cores (one process per core, each on a bounded sample of the same
+recipe).
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
+import hashlib
 import json
-import math
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -31,7 +40,16 @@ sys.path.insert(0, ROOT)
 METRIC = "B-char cell-steps/s on 1 GB300 (plain vs batched/served); p50/p99 solve latency"
 UNIT = "cell-steps/s"
 WORKLOAD = "vortex2d_1024"
-ORACLE_SAMPLE_N = 128  # cells per axis of the oracle's bounded sample (same recipe)
+ORACLE_SAMPLE_N = 128  # cells per axis of each oracle process's sample (same recipe)
+# DRAM bytes per launch of kernels, measured by ncu on a named workload, each
+# with the hash of the kernel's source when it was measured (a line whose hash
+# no longer matches is ignored: the kernel changed since)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "vortex2d_1024_dram_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_1908_05834_gb300", "csrc")
+# the file holding each kernel, and the definitions its source hash covers
+# besides the kernel itself (its line-sum epilogue; the tile loop it runs)
+KERNEL_FILES = {"k_spmv": ("sparse.cu", ["struct SpmvEpi"]), "k_scale_tiles": ("sparse.cu", ["struct ScaleEpi"]),
+                "k_cg_matvec": ("sparse.cu", ["struct MatvecEpi"])}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -62,6 +80,60 @@ def _peaks():
             p = json.load(f)
         return float(p["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _definition(text: str, head: str) -> str:
+    """The source of the definition starting at `head` (through the brace
+    that closes its body)."""
+    i = text.index(head)
+    j = text.index("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[k], 0)
+        if depth == 0:
+            return text[i:k + 1]
+    raise ValueError(head)
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of a kernel's definition, the definitions it depends on and the
+    tile loop header: what its DRAM traffic depends on."""
+    fname, deps = KERNEL_FILES[kernel]
+    with open(os.path.join(CSRC, fname)) as f:
+        text = f.read()
+    with open(os.path.join(CSRC, "tiles.cuh")) as f:
+        tiles = f.read()
+    h = hashlib.sha256()
+    for head in [f"__global__ void {kernel}("] + deps:
+        h.update(_definition(text, head).encode())
+    h.update(tiles.encode())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """(DRAM bytes per launch, the line) for kernel on workload from the traffic
+    file, or (None, None) when absent or taken on other sources."""
+    if not os.path.exists(TRAFFIC_FILE) or kernel not in KERNEL_FILES:
+        return None, None
+    want = kernel_source_hash(kernel)
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+                if parts[3] == want:
+                    return int(float(parts[2])), line.strip()
+    return None, None
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -114,24 +186,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(stage: str, nc: int, nnz: int) -> int:
-    """Bytes one launch of a stage must move at minimum (the per-unit figures
-    of the design notes times the units of one launch)."""
-    if stage == "cg_matvec":
-        # per entry, once through the row view and once through the column
-        # view: column/row index 4 B + a^2 8 B; per node (2 nc): pointer 8 B,
-        # diagonal 8 B, p read 8 B, q write 8 B
-        return nnz * 2 * (4 + 8) + 2 * nc * (8 + 8 + 8 + 8)
-    if stage == "smooth":
-        # one FP32 damped-Jacobi sweep of the finest multigrid level: 2 nc
-        # nodes, 2 nnz off-diagonal entries (value 4 B + column 4 B); per node
-        # pointer 8 B, x, b, diagonal read and x_out written (4 B each)
-        return 2 * nnz * (4 + 4) + 2 * nc * (8 + 4 * 4)
+def algorithmic_bytes(stage: str, nc: int, nnz: int, c_bytes: int = 8) -> int:
+    """Bytes one launch of a stage must move at least: per entry and per node
+    (cell, or constraint node of the minimisation: 2 n_c of them), each
+    array read or written once; gathered vectors count once (they stay in L2)."""
     if stage == "update":
-        # per entry: column 4 B + weight 8 B; per cell: row pointer 8 B,
-        # c_in 8 B, c_out 8 B, |K|_phi 8 B
-        return nnz * (4 + 8) + nc * (8 + 8 + 8 + 8)
+        # c^{n+1} = W c^n and the mass sums: per entry column 4 B + weight 8 B;
+        # per cell row pointer 8 B, c_in and c_out, |K|_phi 8 B
+        return nnz * (4 + 8) + nc * (8 + 2 * c_bytes + 8)
+    if stage == "scaling":
+        # one column and one row pass of eq. volAdj, each over its own view of
+        # the entries (index 4 B + value 8 B); per line pointer 8 B, target 8 B,
+        # the other side's factor 8 B, own factor written 8 B
+        return 2 * (nnz * (4 + 8) + nc * (8 + 8 + 8 + 8))
+    if stage == "cg_matvec":
+        # the minimisation's product with A-hat D A-hat^T + diag: once through
+        # the row view and once through the column view (index 4 B + a^2 D 8 B
+        # per entry); per node (2 n_c) pointer 8 B, diagonal 8 B, p 8 B, q 8 B
+        return 2 * nnz * (4 + 8) + 2 * nc * (8 + 8 + 8 + 8)
+    if stage == "smooth":
+        # one damped-Jacobi sweep of the multigrid's finest level: 2 n_c nodes,
+        # 2 nnz off-diagonal entries (value 8 B + column 4 B); per node pointer
+        # 8 B, x, b, diagonal and weight read and x_out written (8 B each)
+        return 2 * nnz * (8 + 4) + 2 * nc * (8 + 5 * 8)
     raise KeyError(stage)
+
+
+def _face_tensors(wl, st, device=None, pinned=False):
+    import torch
+    out = []
+    for a in wl.faces(st % wl.steps):
+        t = torch.from_numpy(np.ascontiguousarray(a).reshape(-1))
+        out.append(t.to(device) if device is not None else (t.pin_memory() if pinned else t))
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -149,12 +236,11 @@ def run_ours(args, rank, world, local_rank):
     wl = inputs.workload(args.workload, n=args.n)
     nc = wl.nc
     nsteps = args.warmup + args.steps
-    faces_dev = []
-    for st in range(nsteps):
-        f = wl.faces(st % wl.steps)
-        faces_dev.append([torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev) for a in f])
-    opts = bchar.default_options(precision=bchar.FP32_SPLIT if wl.precision == "fp32split" else bchar.FP64,
-                                 qp_max_iter=args.qp_max_iter, qp_tol=args.qp_tol)
+    faces_dev = [_face_tensors(wl, st, dev) for st in range(nsteps)]
+    extra = {} if args.qp_tol is None else {"qp_tol": args.qp_tol}
+    if args.qp_max_refine is not None:
+        extra["qp_max_refine"] = args.qp_max_refine
+    opts = bchar.default_options(precision=bchar.FP32_SPLIT if wl.precision == "fp32split" else bchar.FP64, **extra)
     mesh = bchar.Mesh(wl.coords, wl.phi, opts)
     cdt = torch.float32 if wl.c_dtype == "f32" else torch.float64
     c = torch.tensor(wl.c0, dtype=cdt, device=dev)
@@ -172,11 +258,13 @@ def run_ours(args, rank, world, local_rank):
     for st in range(args.warmup):
         one(st)
     torch.cuda.synchronize()
+    c_at_timed = c.cpu()  # the end-to-end run repeats the timed steps from here
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     sampler = ClockSampler(local_rank)
-    sampler.start()
+    if not args.profile:
+        sampler.start()
     times, infos = [], []
     for k in range(args.steps):
         flush.zero_()
@@ -191,78 +279,86 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     total = max_over_ranks(sum(times), dev)
     value = whole_job_rate(nc, args.steps, world, total)
-
-    # dominant kernel: live CUDA-event timing of the stages on the last step's data
     last = infos[-1]
-    # the NVTX range lets a profiler select these replays (ncu --nvtx --nvtx-include stage_timing/)
+    nnz = last["nnz"]
+    cb = 4 if wl.c_dtype == "f32" else 8
+
+    # kernel timings: CUDA events around graph replays of each stage's kernels on
+    # the handle's stream, on the last step's data
     torch.cuda.nvtx.range_push("stage_timing")
-    stage_ms = {
-        "smooth": mesh.time_stage(bchar.STAGE_SMOOTH, 50),
-        "cg_matvec": mesh.time_stage(bchar.STAGE_CG_MATVEC, 50),
-        "update": mesh.time_stage(bchar.STAGE_UPDATE, 50),
-        "assemble": mesh.time_stage(bchar.STAGE_ASSEMBLE, 5),
-        "track": mesh.time_stage(bchar.STAGE_TRACK, 5),
-    }
+    ms = {"update": mesh.time_stage(bchar.STAGE_UPDATE, 50), "scaling": mesh.time_stage(bchar.STAGE_SCALING, 20),
+          "cg_matvec": mesh.time_stage(bchar.STAGE_CG_MATVEC, 50),
+          "assemble": mesh.time_stage(bchar.STAGE_ASSEMBLE, 3), "track": mesh.time_stage(bchar.STAGE_TRACK, 3)}
+    if last["amg_levels"] > 0:
+        ms["smooth"] = mesh.time_stage(bchar.STAGE_SMOOTH, 50)
+        ms["vcycle"] = mesh.time_stage(bchar.STAGE_VCYCLE, 20)
     torch.cuda.nvtx.range_pop()
     cg_mean = statistics.mean(i["cg_iters"] for i in infos)
-    step_stage_ms = {k: round(statistics.mean(i["ms_stage"][k] for i in infos), 3) for k in infos[0]["ms_stage"]}
-    per_step_ms = {
-        "smooth_level0": stage_ms["smooth"] * 2 * cg_mean,  # the finest level's two passes per V-cycle
-        "cg_matvec": stage_ms["cg_matvec"] * cg_mean,
-        "update": stage_ms["update"],
-        "assemble": stage_ms["assemble"],
-        "track": stage_ms["track"],
-    }
+    # launches per step of each streaming kernel: the update once, the scalings
+    # N = 10 times (a column and a row pass each), the matvec once per CG
+    # iteration, and the finest level's post-smoothing sweep once per V-cycle
+    # (one V-cycle per CG iteration)
+    per_step = {"update": 1, "scaling": opts.n_scale, "cg_matvec": cg_mean, "smooth": cg_mean}
     hbm, peak_kind = _peaks()
-    sm_bytes = algorithmic_bytes("smooth", nc, last["nnz"])
-    achieved = sm_bytes / (stage_ms["smooth"] * 1e-3) / 1e9
-    mv_bytes = algorithmic_bytes("cg_matvec", nc, last["nnz"])
-    # DRAM bytes of one finest-level sweep from an ncu capture of the same kernel
-    # on the 512x512 case of this recipe (profiles/k_jacobi_vortex2d_512.md:
-    # 23.92 MB read, no write reaching DRAM), scaled by cells to this launch
-    traffic = round(23.921408e6 / (512 * 512) * nc) if args.workload == WORKLOAD else None
-    roofline = {"bound": "hbm", "kernel": "k_jacobi<float> (finest multigrid level, post-smoothing)",
-                "achieved": round(achieved, 1),
-                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "traffic_note": "dram read+write per launch, ncu capture at 512x512 scaled by cells" if traffic else None,
-                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": sm_bytes,
-                "mean_launch_ms": round(stage_ms["smooth"], 5),
-                "k_cg_matvec": {"achieved": round(mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9, 1),
-                                "frac": round(mv_bytes / (stage_ms["cg_matvec"] * 1e-3) / 1e9 / hbm, 4),
-                                "algorithmic_bytes_per_launch": mv_bytes,
-                                "mean_launch_ms": round(stage_ms["cg_matvec"], 5)}}
+    step_ms = 1e3 * total / args.steps
+    kernels = {}
+    names = {"update": "k_spmv", "scaling": "k_scale_tiles", "cg_matvec": "k_cg_matvec",
+             "smooth": "k_jacobi<double> (finest multigrid level)"}
+    for stage in ("update", "scaling", "cg_matvec", "smooth"):
+        if stage not in ms:
+            continue
+        byt = algorithmic_bytes(stage, nc, nnz, cb)
+        gbs = byt / (ms[stage] * 1e-3) / 1e9
+        kernels[stage] = {"kernel": names[stage], "algorithmic_bytes_per_launch": byt,
+                          "mean_launch_ms": round(ms[stage], 5), "achieved": round(gbs, 1),
+                          "frac": round(gbs / hbm, 4), "launches_per_step": round(per_step[stage], 1),
+                          "share_of_step": round(ms[stage] * per_step[stage] / step_ms, 4)}
+    # the roofline kernel: the largest share of the step among the kernels of the
+    # method's own stages (the update, the scalings, the minimisation's product);
+    # the multigrid smoother, the preconditioner's kernel, is listed beside them
+    dom = max(("update", "scaling", "cg_matvec"), key=lambda k: kernels[k]["share_of_step"])
+    K = kernels[dom]
+    traffic, traffic_line = measured_traffic(K["kernel"], args.workload)
+    roofline = {"bound": "hbm", "kernel": K["kernel"], "stage": dom, "achieved": K["achieved"], "peak": hbm,
+                "unit": "GB/s", "frac": K["frac"], "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: " + traffic_line)
+                if traffic else "no ncu capture of the current kernel source",
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "algorithmic_bytes_per_launch": K["algorithmic_bytes_per_launch"],
+                "mean_launch_ms": K["mean_launch_ms"], "share_of_step": K["share_of_step"],
+                "all_streaming_kernels": kernels}
 
-    # end to end through the public API with host buffers
-    e2e = run_e2e(args, mesh, wl, bchar, torch, dev)
+    e2e = None if args.profile else run_e2e(args, mesh, wl, bchar, torch, dev, c_at_timed)
 
-    # plain vs batched, and the serving loop (one GPU; replicas at N > 1 are not re-measured)
     batched = served = None
-    if world == 1 and not args.no_serve:
+    if world == 1 and not args.no_serve and not args.profile:
         batched = run_batched(args, torch, bchar, inputs)
         served = run_served(args, torch, bchar, inputs)
 
+    step_stage_ms = {k: round(statistics.mean(i["ms_stage"][k] for i in infos), 3) for k in infos[0]["ms_stage"]}
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded analytic fields and meshes)",
         "config": {"workload": f"{args.workload}: {inputs.describe(args.workload, args.n)}",
-                   "cells": nc, "cells_per_axis": len(wl.coords[0]) - 1, "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps",
-                   "qp_tol": args.qp_tol, "qp_max_iter": args.qp_max_iter,
-                   "qp_note": "the minimisation is solved to qp_tol (relative L1 optimality residual); global mass "
-                              "is exact regardless (final column scaling); qp_converged counts the steps that "
-                              "reached qp_tol within qp_max_iter"},
-        "gpu_launches": int(statistics.mean(i["kernel_launches"] for i in infos) * args.steps) + 0,
+                   "cells": nc, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) between steps; inputs also exceed L2",
+                   "qp_tol": opts.qp_tol, "qp_max_refine": opts.qp_max_refine, "qp_note": "the bounded minimisation is solved to the library default "
+                   "(scaled constraint residual <= qp_tol, mean complementarity <= 1e-12), the tolerance the "
+                   "parity tests use; qp_converged counts the timed steps that met it"},
+        "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "roofline": roofline,
-        "stage_ms_per_step": {k: round(v, 3) for k, v in per_step_ms.items()},
+        "stage_ms": {k: round(v, 4) for k, v in ms.items()},
         "step_stage_ms": step_stage_ms,
-        "step_stats": {"cg_iters_mean": statistics.mean(i["cg_iters"] for i in infos),
+        "step_stats": {"ip_iters": [i["ip_iters"] for i in infos], "cg_iters": [i["cg_iters"] for i in infos],
                        "qp_converged": sum(i["qp_converged"] for i in infos),
                        "kkt_rel_max": max(i["kkt_rel"] for i in infos),
                        "max_rel_row_res_max": max(i["max_rel_row_res"] for i in infos),
-                       "amg_levels": last["amg_levels"], "amg_coarsest": last["amg_coarsest"], "nnz": last["nnz"],
-                       "row_cap": last["row_cap"],
-                       "substeps": last["substeps"],
+                       "max_rel_col_res_max": max(i["max_rel_col_res"] for i in infos),
+                       "n_at_bounds": [i["n_at_bounds"] for i in infos],
+                       "amg_levels": last["amg_levels"], "amg_coarsest": last["amg_coarsest"], "nnz": nnz,
+                       "row_cap": last["row_cap"], "spill_rows": last["spill_rows"], "substeps": last["substeps"],
                        "max_rel_mass_change": max(abs(i["mass_after"] - i["mass_before"]) / i["mass_before"]
                                                   for i in infos)},
         "clocks": clocks,
@@ -273,24 +369,24 @@ def run_ours(args, rank, world, local_rank):
     if served is not None:
         result["served"] = served
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.profile:
             result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(result), flush=True)
     mesh.close()
 
 
-def run_e2e(args, mesh, wl, bchar, torch, dev):
-    """Same metric through the C ABI with HOST buffers: every step copies the
-    step's face velocities and c to the device and reads c back."""
-    k = max(1, min(args.steps, 2))
-    faces_host = [[torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).pin_memory() for a in wl.faces(st % wl.steps)]
-                  for st in range(k)]
-    cdt = torch.float32 if wl.c_dtype == "f32" else torch.float64
-    c_host = torch.tensor(wl.c0, dtype=cdt).pin_memory()
+def run_e2e(args, mesh, wl, bchar, torch, dev, c_start):
+    """The same steps as the device-timed run, through the C ABI with HOST
+    buffers: every step passes the step's face velocities from pinned host
+    memory (the library copies them), copies c to the device and reads the new
+    c back; the clock (host, around the whole loop) includes all of it."""
+    k0, k = args.warmup, args.steps
+    faces_host = [_face_tensors(wl, k0 + st, pinned=True) for st in range(k)]
+    c_host = c_start.clone().pin_memory()
     back = torch.empty_like(c_host).pin_memory()
-    c_dev = torch.empty(wl.nc, dtype=cdt, device=dev)
+    c_dev = torch.empty(wl.nc, dtype=c_host.dtype, device=dev)
     out = torch.empty_like(c_dev)
-    h2d = sum(f.numel() * 8 for f in faces_host[0]) + c_host.numel() * c_host.element_size()
+    h2d = sum(f.numel() * f.element_size() for f in faces_host[0]) + c_host.numel() * c_host.element_size()
     d2h = back.numel() * back.element_size()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -303,22 +399,33 @@ def run_e2e(args, mesh, wl, bchar, torch, dev):
         c_host.copy_(back)
     t = time.perf_counter() - t0
     return {"value": round(wl.nc * k / t, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": k}
+            "d2h_bytes_per_step": int(d2h), "steps": k, "step_indices": [k0, k0 + k - 1]}
 
 
-def _serving_options(bchar, args):
-    return bchar.default_options(precision=bchar.FP32_SPLIT, qp_tol=args.qp_tol, qp_max_iter=args.qp_max_iter)
+def _serving_sample(inputs, count, max_cells, steps):
+    """The first `count` requests of the serving stream with at most max_cells
+    cells, each cut to `steps` steps (a bounded sample of the stream)."""
+    picked = []
+    for r in inputs.serving_requests(512):
+        if r.nc <= max_cells:
+            picked.append(dataclasses.replace(r, steps=min(r.steps, steps)))
+        if len(picked) == count:
+            break
+    return picked
+
+
+def _serving_options(bchar):
+    return bchar.default_options(precision=bchar.FP32_SPLIT)
 
 
 def run_batched(args, torch, bchar, inputs):
-    """Plain vs batched stepping of the first --batch-count meshes of the
-    serving stream (uneven sizes), --batch-steps steps each after one warm-up
-    step: plain = one bchar_step after another; batched = bchar_step_batch of
-    all instances per step.  Host wall clock around whole steps (every
+    """Plain vs batched stepping of a sample of the serving stream (uneven
+    sizes): plain = one bchar_step after another; batched = bchar_step_batch
+    of all instances per step.  Host wall clock around whole steps (every
     instance's step has finished when the call returns)."""
-    reqs = inputs.serving_requests(args.batch_count)
+    reqs = _serving_sample(inputs, args.batch_count, args.serve_max_cells, args.batch_steps + 1)
     prepared = [r.materialize() for r in reqs]
-    opts = _serving_options(bchar, args)
+    opts = _serving_options(bchar)
 
     def make():
         hs = []
@@ -344,8 +451,7 @@ def run_batched(args, torch, bchar, inputs):
         for h in hs:
             h[2], h[3] = h[3], h[2]
 
-    out = {}
-    finals = {}
+    out, finals = {}, {}
     for mode, fn in (("plain", plain_step), ("batched", batch_step)):
         hs = make()
         fn(hs, 0)
@@ -362,24 +468,24 @@ def run_batched(args, torch, bchar, inputs):
     same = all(torch.equal(a, b) for a, b in zip(finals["plain"], finals["batched"]))
     return {"plain": out["plain"], "batched": out["batched"], "unit": UNIT,
             "speedup": round(out["batched"] / out["plain"], 3), "bitwise_equal": same,
-            "instances": len(reqs), "steps": args.batch_steps,
-            "cells": [r.nc for r in reqs],
-            "sample": f"meshes of the first {len(reqs)} requests of the serving stream (seed 4004), "
-                      f"{args.batch_steps} timed steps after 1 warm-up step, FP32 split, qp_tol {args.qp_tol}"}
+            "instances": len(reqs), "steps": args.batch_steps, "cells": [r.nc for r in reqs],
+            "sample": f"the first {len(reqs)} requests of the serving stream (seed 4004) with at most "
+                      f"{args.serve_max_cells} cells, {args.batch_steps} timed steps after 1 warm-up step, "
+                      f"FP32 split, library-default minimisation tolerance"}
 
 
 def run_served(args, torch, bchar, inputs):
-    """The first --serve-requests requests of the serving stream (Poisson
-    arrivals, mean gap 2 ms, 60 % 2D / 40 % 3D, 10-100 steps) through the
-    serving loop: 120 GB admission budget, --serve-slots concurrent requests.
-    The payloads (mesh, phi, base field, c0) are built before the clock
-    starts; latency = finish - arrival, including queueing and the uploads."""
+    """A sample of the serving stream (Poisson arrivals, mean gap 2 ms, 60 % 2D /
+    40 % 3D) through the serving loop: 120 GB admission budget, --serve-slots
+    concurrent requests.  The payloads (mesh, phi, base field, c0) are built
+    before the clock starts; latency = finish - arrival, including queueing and
+    the uploads."""
     from paper_1908_05834_gb300 import serve
-    reqs = inputs.serving_requests(args.serve_requests)
+    reqs = _serving_sample(inputs, args.serve_requests, args.serve_max_cells, args.serve_steps)
     t0 = time.perf_counter()
     prepared = {r.rid: r.materialize() for r in reqs}
     prep_s = time.perf_counter() - t0
-    opts = _serving_options(bchar, args)
+    opts = _serving_options(bchar)
     srv = serve.Server(serve.GpuExecutor(prepared, opts, torch.cuda.current_device()),
                        serve.estimator_for(prepared, opts), budget_bytes=120e9, max_active=args.serve_slots)
     res = srv.run(reqs)
@@ -388,68 +494,118 @@ def run_served(args, torch, bchar, inputs):
               "peak_admitted_gb": round(srv.peak_used / 1e9, 2), "peak_active": srv.peak_active,
               "max_peak_bytes_over_estimate": round(max((r.peak_bytes / r.est_bytes) for r in res
                                                         if r.status == "ok"), 3),
-              "footprint_overruns": len(srv.overruns),  # requests charged above their estimate
+              "footprint_overruns": len(srv.overruns),
               "prep_s": round(prep_s, 1),
-              "sample": f"first {len(reqs)} of the 512-request serving stream (seed 4004), full step counts, "
-                        f"FP32 split, qp_tol {args.qp_tol}"})
+              "sample": f"the first {len(reqs)} requests of the 512-request serving stream (seed 4004) with at "
+                        f"most {args.serve_max_cells} cells, each cut to {args.serve_steps} steps, FP32 split, "
+                        f"library-default minimisation tolerance"})
     return s
 
 
-def oracle_sample_step_rate(seconds: float):
-    """The FP64 CPU oracle as it stands, timed on this host, on a bounded
-    sample of the workload: the same recipe at ORACLE_SAMPLE_N^2 cells,
-    consecutive steps until about `seconds` of CPU time."""
+# ---------------------------------------------------------------- the oracle on the host cores
+
+_W = {}
+
+
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_worker_init(n):
+    sys.path.insert(0, ROOT)
     import oracle
     from paper_1908_05834_gb300 import inputs
-    wl = inputs.workload(WORKLOAD, n=ORACLE_SAMPLE_N)
-    mesh = oracle.Mesh(wl.coords, wl.phi)
-    oracle.build_oracle()
-    c = wl.c0.astype(np.float64)
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        r = oracle.step(mesh, wl.faces(steps % wl.steps), wl.dt, c)
-        c = r["c"]
-        steps += 1
-        if time.perf_counter() - t0 >= seconds or steps >= 50:
-            break
-    t = time.perf_counter() - t0
-    return wl.nc * steps / t, steps, t, wl.nc
+    wl = inputs.workload(WORKLOAD, n=n)
+    _W["wl"] = wl
+    _W["mesh"] = oracle.Mesh(wl.coords, wl.phi)
+    _W["c"] = wl.c0.astype(np.float64)
+
+
+def _oracle_worker_step(k):
+    import oracle
+    wl = _W["wl"]
+    t = time.perf_counter()
+    r = oracle.step(_W["mesh"], wl.faces(k % wl.steps), wl.dt, _W["c"])
+    _W["c"] = r["c"]
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """One oracle process per host core (spawned), each stepping its own copy
+    of the bounded sample: the recipe at ORACLE_SAMPLE_N^d cells."""
+
+    def __init__(self, procs: int | None = None):
+        import oracle
+        oracle.build_oracle()  # once, before the workers load it
+        self.procs = procs or len(os.sched_getaffinity(0))
+        # one BLAS thread per process (the processes already cover the cores): the
+        # spawned interpreters read these when they first import numpy
+        saved = {v: os.environ.get(v) for v in _ONE_THREAD}
+        os.environ.update({v: "1" for v in _ONE_THREAD})
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_worker_init,
+                                                     initargs=(ORACLE_SAMPLE_N,))
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        from paper_1908_05834_gb300 import inputs
+        self.cells = inputs.workload(WORKLOAD, n=ORACLE_SAMPLE_N).nc
+
+    def step(self, k: int) -> float:
+        """Step k on every process; returns the wall time."""
+        t = time.perf_counter()
+        self.pool.map(_oracle_worker_step, [k] * self.procs, chunksize=1)
+        return time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def sample_text(self, steps: int, seconds: float) -> str:
+        return (f"{self.procs} processes (one per host core, {cpu_model()}), each stepping its own copy of the "
+                f"same recipe at {ORACLE_SAMPLE_N}x{ORACLE_SAMPLE_N} ({self.cells} cells) for {steps} steps, "
+                f"{seconds:.1f} s wall; serial C + numpy/scipy (SuperLU) per process")
 
 
 def cpu_baseline(seconds: float):
-    rate, steps, t, nc = oracle_sample_step_rate(seconds)
-    return {"value": round(rate, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} consecutive steps of the same recipe at {ORACLE_SAMPLE_N}x{ORACLE_SAMPLE_N} "
-                      f"({nc} cells), {t:.1f} s, serial C + numpy/scipy (SuperLU)"}
+    pool = OraclePool()
+    try:
+        pool.step(0)  # warm-up (imports, first factorisation)
+        t, k = 0.0, 0
+        while t < seconds and k < 20:
+            t += pool.step(1 + k)
+            k += 1
+    finally:
+        pool.close()
+    rate = pool.cells * pool.procs * k / t
+    return {"value": round(rate, 1), "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+            "sample": pool.sample_text(k, t)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    # each step of --steps/--warmup is one oracle step on the bounded sample
-    import oracle
-    from paper_1908_05834_gb300 import inputs
-    wl = inputs.workload(WORKLOAD, n=ORACLE_SAMPLE_N)
-    mesh = oracle.Mesh(wl.coords, wl.phi)
-    oracle.build_oracle()
-    c = wl.c0.astype(np.float64)
-    for st in range(args.warmup):
-        c = oracle.step(mesh, wl.faces(st % wl.steps), wl.dt, c)["c"]
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        c = oracle.step(mesh, wl.faces((args.warmup + k) % wl.steps), wl.dt, c)["c"]
-    t = time.perf_counter() - t0
-    value = wl.nc * args.steps / t
-    sample = (f"{args.steps} steps of the same recipe at {ORACLE_SAMPLE_N}x{ORACLE_SAMPLE_N} ({wl.nc} cells), "
-              f"serial C + numpy/scipy (SuperLU)")
+    pool = OraclePool()
+    try:
+        for st in range(args.warmup):
+            pool.step(st)
+        t = 0.0
+        for k in range(args.steps):
+            t += pool.step(args.warmup + k)
+    finally:
+        pool.close()
+    value = pool.cells * pool.procs * args.steps / t
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded analytic fields and meshes)",
-        "config": {"workload": f"{WORKLOAD} recipe, oracle sample at {ORACLE_SAMPLE_N}^2", "cells": wl.nc},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"{WORKLOAD} recipe, oracle sample at {ORACLE_SAMPLE_N}^2 per process",
+                   "cells": pool.cells * pool.procs},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                         "sample": pool.sample_text(args.steps, t)},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -457,20 +613,26 @@ def run_reference(args, rank, world):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--n", type=int, default=None, help="cells per axis (same recipe; for small profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--qp-max-iter", type=int, default=30000)
-    p.add_argument("--qp-tol", type=float, default=1e-5)
-    p.add_argument("--n", type=int, default=None, help="cells per axis (same recipe; for small profiling runs)")
+    p.add_argument("--qp-tol", type=float, default=None, help="default: the library's default")
+    p.add_argument("--qp-max-refine", type=int, default=None,
+                   help="cap on interior-point iterations (default: the library's); for short profiling runs")
     p.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
-    p.add_argument("--batch-count", type=int, default=16)
-    p.add_argument("--batch-steps", type=int, default=3)
-    p.add_argument("--serve-requests", type=int, default=32)
-    p.add_argument("--serve-slots", type=int, default=32)
+    p.add_argument("--batch-count", type=int, default=8)
+    p.add_argument("--batch-steps", type=int, default=2)
+    p.add_argument("--serve-requests", type=int, default=12)
+    p.add_argument("--serve-steps", type=int, default=3)
+    p.add_argument("--serve-slots", type=int, default=12)
+    p.add_argument("--serve-max-cells", type=int, default=150000)
+    p.add_argument("--profile", action="store_true",
+                   help="a run to capture under a profiler: the steps and the stage replays only (no clock "
+                        "sampling subprocess, no end-to-end, serving or CPU runs); its line is not a bench result")
     args = p.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":

@@ -68,7 +68,7 @@ typedef struct {
                            its target (1e-9), the mean complementarity is <= 1e-12 and the
                            stationarity residuals are <= 1e-12 of the largest multiplier */
     int qp_max_iter;    /* cap on conjugate-gradient iterations of one step, all solves (200000) */
-    int qp_max_refine;  /* cap on interior-point iterations of one step (100) */
+    int qp_max_refine;  /* cap on interior-point iterations of one step (300) */
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
     int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
                            1 = aggregation multigrid (default), 0 = Jacobi */
@@ -208,9 +208,9 @@ enum {
     BCHAR_STAGE_UPDATE = 1,    /* c^{n+1} = W c^n and the mass sums */
     BCHAR_STAGE_ASSEMBLE = 2,  /* ball intersections and row assembly into the slab */
     BCHAR_STAGE_TRACK = 3,     /* RK4 tracking of all balls */
-    BCHAR_STAGE_SMOOTH = 4,    /* one FP32 damped-Jacobi sweep of the multigrid's finest level */
+    BCHAR_STAGE_SMOOTH = 4,    /* one damped-Jacobi sweep of the multigrid's finest level */
     BCHAR_STAGE_SCALING = 5,   /* one column and one row scaling of eq. volAdj (on scratch copies) */
-    BCHAR_STAGE_VCYCLE = 6     /* one FP32 V-cycle of the multigrid preconditioner (the last one built) */
+    BCHAR_STAGE_VCYCLE = 6     /* one V-cycle of the multigrid preconditioner (the last one built) */
 };
 
 /* Measurement aid: replay the kernel of one stage `reps` times on the data of

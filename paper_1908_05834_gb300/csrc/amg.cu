@@ -626,15 +626,32 @@ static void coarse_fill(bchar_mesh_t m, const AmgLevel &F, AmgLevel &C, int64_t 
 
 // ---------------------------------------------------------------- V-cycle kernels
 //
-// The V-cycle runs on a copy of each level's operator divided by a fixed
-// scale (the square of the largest |K|_phi, so that the entries sit near 1),
-// in FP32 while the residual is large (it is only a preconditioner, the
-// conjugate gradients around it stay in FP64, and on this GPU FP32 arithmetic
-// is far faster than FP64) and in FP64 for the last digits.
+// The V-cycle runs in FP64 on a copy of each level's operator divided by a
+// fixed scale (the square of the largest |K|_phi, so that the entries sit near
+// 1).  An FP32 V-cycle costs less per application but loses the modes the
+// preconditioner exists for: a cluster held by a shift ~1e-10 of its diagonal
+// has a residual that cancels below FP32 rounding in b - L x, and the
+// conjugate gradients then need more than twice the iterations (measured on
+// the 1024^2 and 128^3 workloads), which costs more than FP64 saves.  The
+// kernels are templates on the precision all the same.
 
 template <class T> __global__ void k_scaled_copy(int64_t n, const double *in, T *out, double inv_scale) {
     dep_enter();
     GRID_STRIDE(i, n) out[i] = static_cast<T>(in[i] * inv_scale);
+}
+
+// Relaxation weight of row i: kOmega, or 1 for a row without off-diagonal
+// entries (then one sweep solves its equation exactly).
+__device__ __forceinline__ double row_weight(const int64_t *ptr, int64_t i) {
+    return ptr[i + 1] == ptr[i] ? 1.0 : kOmega;
+}
+
+// w_i = omega_i / (diag_i / scale): kOmega, or 1 for a row without
+// off-diagonal entries (one sweep then solves its equation exactly)
+template <class T>
+__global__ void k_scaled_inv(int64_t n, const int64_t *ptr, const double *diag, T *out, double inv_scale) {
+    dep_enter();
+    GRID_STRIDE(i, n) out[i] = static_cast<T>(row_weight(ptr, i) / (diag[i] * inv_scale));
 }
 
 // b = S res (S: +1 rows, -1 columns), in the V-cycle's precision
@@ -677,52 +694,48 @@ __global__ void k_flip_out_dots(int64_t nc, const T *x, double inv_scale, double
     }
 }
 
-// Relaxation weight of row i: kOmega, or 1 for a row without off-diagonal
-// entries (then one sweep solves its equation exactly).
-__device__ __forceinline__ double row_weight(const int64_t *ptr, int64_t i) {
-    return ptr[i + 1] == ptr[i] ? 1.0 : kOmega;
-}
 
-// x = omega_i b / diag
-template <class T>
-__global__ void k_jacobi0(int64_t n, const int64_t *ptr, const T *diag, const T *b, T *x, const CgState *st) {
+// The smoothers multiply by w_i = omega_i / diag_i, formed once per build
+// (k_scaled_inv): a division per node (and, in the pre-smoothing, per entry)
+// would cost far more, in FP64 above all.
+
+// x = w b
+template <class T> __global__ void k_jacobi0(int64_t n, const T *dinv, const T *b, T *x, const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
-    GRID_STRIDE(i, n) x[i] = static_cast<T>(row_weight(ptr, i)) * b[i] / diag[i];
+    GRID_STRIDE(i, n) x[i] = dinv[i] * b[i];
 }
 
-// x_out = x + omega_i (b - L x) / diag
+// x_out = x + w (b - L x)
 template <class T>
-__global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag, const T *x,
-                         const T *b, T *x_out, const CgState *st) {
+__global__ void k_jacobi(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
+                         const T *dinv, const T *x, const T *b, T *x_out, const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int64_t e0 = ptr[i], e1 = ptr[i + 1];
         T s = diag[i] * x[i];
         for (int64_t e = e0; e < e1; ++e) s += val[e] * x[col[e]];
-        const T om = static_cast<T>(e1 == e0 ? 1.0 : kOmega);
-        x_out[i] = x[i] + om * (b[i] - s) / diag[i];
+        x_out[i] = x[i] + dinv[i] * (b[i] - s);
     }
 }
 
-// Pre-smoothing from zero and the residual in one pass: x = omega_i b / diag,
-// r = b - L x.  A neighbour j has an edge, so its weight is kOmega and its x_j
-// is formed from b_j and d_j exactly as its owner forms it.
+// Pre-smoothing from zero and the residual in one pass: x = w b, r = b - L x
+// (a neighbour's x_j = w_j b_j is formed exactly as its owner forms it).
 template <class T>
 __global__ void k_presmooth_residual(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
-                                     const T *b, T *x, T *r, const CgState *st) {
+                                     const T *dinv, const T *b, T *x, T *r, const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
     GRID_STRIDE(i, n) {
         const int64_t e0 = ptr[i], e1 = ptr[i + 1];
-        const T bi = b[i], di = diag[i];
-        const T xi = static_cast<T>(e1 == e0 ? 1.0 : kOmega) * bi / di;
+        const T bi = b[i];
+        const T xi = dinv[i] * bi;
         x[i] = xi;
-        T s = di * xi;
+        T s = diag[i] * xi;
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t j = col[e];
-            s += val[e] * (static_cast<T>(kOmega) * b[j] / diag[j]);
+            s += val[e] * (dinv[j] * b[j]);
         }
         r[i] = bi - s;
     }
@@ -730,11 +743,10 @@ __global__ void k_presmooth_residual(int64_t n, const int64_t *ptr, const int32_
 
 // Prolongation and post-smoothing in one pass: with x' = x + xc[agg] (the
 // coarse correction; nothing for a node without a coarse counterpart),
-// x_out = x' + omega_i (b - L x') / diag.  A neighbour's x'_j is formed as its
-// owner forms it (a neighbour has an edge, so it has a coarse counterpart).
+// x_out = x' + w (b - L x').  A neighbour's x'_j is formed as its owner forms it.
 template <class T>
 __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *col, const T *val, const T *diag,
-                                 const int32_t *agg, const T *xc, const T *x, const T *b, T *x_out,
+                                 const T *dinv, const int32_t *agg, const T *xc, const T *x, const T *b, T *x_out,
                                  const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
@@ -748,8 +760,7 @@ __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *c
             const int32_t J = agg[j];  // < 0 only with aggregates kept from an earlier matrix
             s += val[e] * (J >= 0 ? x[j] + xc[J] : x[j]);
         }
-        const T om = static_cast<T>(e1 == e0 ? 1.0 : kOmega);
-        x_out[i] = xi + om * (b[i] - s) / diag[i];
+        x_out[i] = xi + dinv[i] * (b[i] - s);
     }
 }
 
@@ -786,7 +797,7 @@ template <class T> struct SmallLevel {
     int64_t n;
     const int64_t *ptr;
     const int32_t *col;
-    const T *val, *diag;
+    const T *val, *diag, *dinv;
     const int32_t *agg;    // node -> aggregate of the next level (levels above the coarsest)
     const int64_t *mptr;   // members (nodes of the previous level) of each node of this level
     const int32_t *mlist;
@@ -797,18 +808,17 @@ template <class T>
 __global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, int nl, const CgState *st) {
     dep_enter();
     if (st && st->converged) return;
-    const T om = static_cast<T>(kOmega);
     for (int l = 0; l + 1 < nl; ++l) {  // down
         const SmallLevel<T> &L = Ls[l];
         for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x) {
             const int64_t e0 = L.ptr[i], e1 = L.ptr[i + 1];
-            const T bi = L.b[i], di = L.diag[i];
-            const T xi = static_cast<T>(e1 == e0 ? 1.0 : kOmega) * bi / di;
+            const T bi = L.b[i];
+            const T xi = L.dinv[i] * bi;
             L.x[i] = xi;
-            T sum = di * xi;
+            T sum = L.diag[i] * xi;
             for (int64_t e = e0; e < e1; ++e) {
                 const int32_t j = L.col[e];
-                sum += L.val[e] * (om * L.b[j] / L.diag[j]);
+                sum += L.val[e] * (L.dinv[j] * L.b[j]);
             }
             L.r[i] = bi - sum;
         }
@@ -824,7 +834,7 @@ __global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, i
     {  // coarsest
         const SmallLevel<T> &L = Ls[nl - 1];
         for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x)
-            L.x[i] = static_cast<T>(row_weight(L.ptr, i)) * L.b[i] / L.diag[i];
+            L.x[i] = L.dinv[i] * L.b[i];
         __syncthreads();
         for (int k = 0; k < kCoarsestSweeps; ++k) {
             const T *xi = (k & 1) ? L.x2 : L.x;
@@ -832,7 +842,7 @@ __global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, i
             for (int64_t i = threadIdx.x; i < L.n; i += blockDim.x) {
                 T sum = L.diag[i] * xi[i];
                 for (int64_t e = L.ptr[i]; e < L.ptr[i + 1]; ++e) sum += L.val[e] * xi[L.col[e]];
-                xo[i] = xi[i] + static_cast<T>(row_weight(L.ptr, i)) * (L.b[i] - sum) / L.diag[i];
+                xo[i] = xi[i] + L.dinv[i] * (L.b[i] - sum);
             }
             __syncthreads();
         }
@@ -850,7 +860,7 @@ __global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, i
                 const int32_t J = L.agg[j];
                 sum += L.val[e] * (J >= 0 ? L.x[j] + xc[J] : L.x[j]);
             }
-            L.x2[i] = xi + static_cast<T>(e1 == e0 ? 1.0 : kOmega) * (L.b[i] - sum) / L.diag[i];
+            L.x2[i] = xi + L.dinv[i] * (L.b[i] - sum);
         }
         __syncthreads();
     }
@@ -861,12 +871,11 @@ __global__ void __launch_bounds__(1024) k_small_cycle(const SmallLevel<T> *Ls, i
 void amg_release(Amg &amg) {
     for (AmgLevel &L : amg.levels) {
         Buf *all[] = {&L.ptr, &L.col, &L.val, &L.diag, &L.exc, &L.agg, &L.mptr, &L.mlist, &L.x, &L.x2, &L.b, &L.r,
-                      &L.fval, &L.fdiag, &L.fx, &L.fx2, &L.fb, &L.fr, &L.dval, &L.ddiag};
+                      &L.dval, &L.ddiag, &L.ddinv};
         for (Buf *b : all) release(*b);
     }
     amg.levels.clear();
     release(amg.tmp);
-    release(amg.small_f);
     release(amg.small_d);
 }
 
@@ -922,26 +931,18 @@ static bool small_descriptors(bchar_mesh_t m, Amg &amg) {
     amg.small_from = from;
     const int nl = amg.nlev - from;
     if (nl == 0) return true;
-    std::vector<SmallLevel<float>> hf(nl);
     std::vector<SmallLevel<double>> hd(nl);
     for (int k = 0; k < nl; ++k) {
         AmgLevel &L = amg.levels[from + k];
         const bool last = from + k == amg.nlev - 1;
         const bool first = k == 0;
-        hf[k] = {L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<float>(L.fval), ptr<float>(L.fdiag),
-                 last ? nullptr : ptr<int32_t>(L.agg), first ? nullptr : ptr<int64_t>(L.mptr),
-                 first ? nullptr : ptr<int32_t>(L.mlist), ptr<float>(L.fx), ptr<float>(L.fx2), ptr<float>(L.fb),
-                 ptr<float>(L.fr)};
-        hd[k] = {L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.dval), ptr<double>(L.ddiag),
+        hd[k] = {L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), ptr<double>(L.dval), ptr<double>(L.ddiag), ptr<double>(L.ddinv),
                  last ? nullptr : ptr<int32_t>(L.agg), first ? nullptr : ptr<int64_t>(L.mptr),
                  first ? nullptr : ptr<int32_t>(L.mlist), ptr<double>(L.x), ptr<double>(L.x2), ptr<double>(L.b),
                  ptr<double>(L.r)};
     }
-    if (!ensure(m, amg.small_f, sizeof(SmallLevel<float>) * nl) ||
-        !ensure(m, amg.small_d, sizeof(SmallLevel<double>) * nl))
-        return false;
-    // pageable sources: the copies have read them when the calls return
-    cudaMemcpyAsync(amg.small_f.p, hf.data(), sizeof(SmallLevel<float>) * nl, cudaMemcpyHostToDevice, m->stream);
+    if (!ensure(m, amg.small_d, sizeof(SmallLevel<double>) * nl)) return false;
+    // a pageable source: the copy has read it when the call returns
     cudaMemcpyAsync(amg.small_d.p, hd.data(), sizeof(SmallLevel<double>) * nl, cudaMemcpyHostToDevice, m->stream);
     return true;
 }
@@ -1075,47 +1076,38 @@ bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
     return amg_scaled_copies(m, amg);
 }
 
-// FP32 and FP64 copies of every level's operator, divided by a fixed scale.
+// The FP64 copy of every level's operator divided by a fixed scale (the
+// square of the largest |K|_phi), and the smoother weights.
 static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg) {
     cudaStream_t s = m->stream;
-    // FP32 copies of every level, divided by the square of the largest |K|_phi
     amg.scale = m->max_volphi * m->max_volphi;
     const double inv = 1.0 / amg.scale;
     for (int l = 0; l < amg.nlev; ++l) {
         AmgLevel &L = amg.levels[l];
         const int64_t nnzl = L.nnz > 0 ? L.nnz : 1;
-        if (!ensure(m, L.fval, sizeof(float) * nnzl) || !ensure(m, L.fdiag, sizeof(float) * L.n) ||
-            !ensure(m, L.fx, sizeof(float) * L.n) || !ensure(m, L.fx2, sizeof(float) * L.n) ||
-            !ensure(m, L.fb, sizeof(float) * L.n) || !ensure(m, L.fr, sizeof(float) * L.n))
+        if (!ensure(m, L.dval, sizeof(double) * nnzl) || !ensure(m, L.ddiag, sizeof(double) * L.n) ||
+            !ensure(m, L.ddinv, sizeof(double) * L.n))
             return false;
-        if (!ensure(m, L.dval, sizeof(double) * nnzl) || !ensure(m, L.ddiag, sizeof(double) * L.n)) return false;
         const double *dg = L.diag_ext ? L.diag_ext : ptr<double>(L.diag);
         if (L.nnz > 0) {
-            launch_dep(k_scaled_copy<float>, blocks_for(L.nnz), kThreads, s, L.nnz, ptr<double>(L.val), ptr<float>(L.fval), inv);
-            launch_dep(k_scaled_copy<double>, blocks_for(L.nnz), kThreads, s, L.nnz, ptr<double>(L.val), ptr<double>(L.dval),
-                                                                         inv);
+            launch_dep(k_scaled_copy<double>, blocks_for(L.nnz), kThreads, s, L.nnz, ptr<double>(L.val),
+                       ptr<double>(L.dval), inv);
+            ++m->launches;
         }
-        launch_dep(k_scaled_copy<float>, blocks_for(L.n), kThreads, s, L.n, dg, ptr<float>(L.fdiag), inv);
         launch_dep(k_scaled_copy<double>, blocks_for(L.n), kThreads, s, L.n, dg, ptr<double>(L.ddiag), inv);
-        m->launches += 4;
+        launch_dep(k_scaled_inv<double>, blocks_for(L.n), kThreads, s, L.n, ptr<int64_t>(L.ptr), dg,
+                   ptr<double>(L.ddinv), inv);
+        m->launches += 2;
     }
     return small_descriptors(m, amg);
 }
 
 // Buffers of one level in the V-cycle's precision.
 template <class T> struct LevelBufs;
-template <> struct LevelBufs<float> {
-    static float *val(AmgLevel &L) { return ptr<float>(L.fval); }
-    static float *diag(AmgLevel &L) { return ptr<float>(L.fdiag); }
-    static float *x(AmgLevel &L) { return ptr<float>(L.fx); }
-    static float *x2(AmgLevel &L) { return ptr<float>(L.fx2); }
-    static float *b(AmgLevel &L) { return ptr<float>(L.fb); }
-    static float *r(AmgLevel &L) { return ptr<float>(L.fr); }
-    static void *small(Amg &a) { return a.small_f.p; }
-};
 template <> struct LevelBufs<double> {
     static double *val(AmgLevel &L) { return ptr<double>(L.dval); }
     static double *diag(AmgLevel &L) { return ptr<double>(L.ddiag); }
+    static double *dinv(AmgLevel &L) { return ptr<double>(L.ddinv); }
     static double *x(AmgLevel &L) { return ptr<double>(L.x); }
     static double *x2(AmgLevel &L) { return ptr<double>(L.x2); }
     static double *b(AmgLevel &L) { return ptr<double>(L.b); }
@@ -1141,7 +1133,7 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
         AmgLevel &C = amg.levels[l + 1];
         const int bl = blocks_for(L.n);
         launch_dep(k_presmooth_residual<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
-                                                        B::diag(L), B::b(L), B::x(L), B::r(L), st);
+                                                        B::diag(L), B::dinv(L), B::b(L), B::x(L), B::r(L), st);
         launch_dep(k_restrict<T>, blocks_for(C.n), kThreads, s, C.n, ptr<int64_t>(C.mptr), ptr<int32_t>(C.mlist), B::r(L),
                                                            B::b(C), st);
         m->launches += 2;
@@ -1153,10 +1145,10 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
     } else {  // a coarsest level too large for one block: Jacobi sweeps from zero (even count: the result is in x)
         AmgLevel &L = amg.levels[amg.nlev - 1];
         const int bl = blocks_for(L.n);
-        launch_dep(k_jacobi0<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), B::diag(L), B::b(L), B::x(L), st);
+        launch_dep(k_jacobi0<T>, bl, kThreads, s, L.n, B::dinv(L), B::b(L), B::x(L), st);
         for (int k = 0; k < amg.large_sweeps; ++k)
             launch_dep(k_jacobi<T>, bl, kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
-                                                B::diag(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
+                                                B::diag(L), B::dinv(L), k & 1 ? B::x2(L) : B::x(L), B::b(L),
                                                 k & 1 ? B::x(L) : B::x2(L), st);
         m->launches += 1 + amg.large_sweeps;
     }
@@ -1168,13 +1160,13 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
         const T *xc = l + 1 == amg.nlev - 1 ? B::x(C) : B::x2(C);
         if (L.n < kFuseBelow) {  // launch-bound levels: one kernel
             launch_dep(k_prolong_smooth<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
-                                                                     B::val(L), B::diag(L), ptr<int32_t>(L.agg), xc,
+                                                                     B::val(L), B::diag(L), B::dinv(L), ptr<int32_t>(L.agg), xc,
                                                                      B::x(L), B::b(L), B::x2(L), st);
             ++m->launches;
         } else {  // large levels: the sweep's neighbours read one array instead of three
             launch_dep(k_prolong<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int32_t>(L.agg), xc, B::x(L), st);
             launch_dep(k_jacobi<T>, blocks_for(L.n), kThreads, s, L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col), B::val(L),
-                                                             B::diag(L), B::x(L), B::b(L), B::x2(L), st);
+                                                             B::diag(L), B::dinv(L), B::x(L), B::b(L), B::x2(L), st);
             m->launches += 2;
         }
     }
@@ -1186,27 +1178,21 @@ static void vcycle(bchar_mesh_t m, Amg &amg, const double *res, double *z, const
     ++m->launches;
 }
 
-// One FP32 damped-Jacobi sweep on the finest level (for timing; on a large
-// finest level this is the V-cycle's post-smoothing kernel).
+// One damped-Jacobi sweep on the finest level (for timing; on a large finest
+// level this is the V-cycle's post-smoothing kernel).
 void amg_smooth_once(bchar_mesh_t m, Amg &amg) {
     AmgLevel &L = amg.levels[0];
-    k_jacobi<float><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
-                                                                  ptr<float>(L.fval), ptr<float>(L.fdiag),
-                                                                  ptr<float>(L.fx), ptr<float>(L.fb),
-                                                                  ptr<float>(L.fx2), nullptr);
+    k_jacobi<double><<<blocks_for(L.n), kThreads, 0, m->stream>>>(L.n, ptr<int64_t>(L.ptr), ptr<int32_t>(L.col),
+                                                                   ptr<double>(L.dval), ptr<double>(L.ddiag),
+                                                                   ptr<double>(L.ddinv), ptr<double>(L.x),
+                                                                   ptr<double>(L.b), ptr<double>(L.x2), nullptr);
 }
 
-void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32, bool b_ready,
+void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool b_ready,
                const double *rp, double *pa, double *pb) {
-    if (fp32)
-        vcycle<float>(m, amg, res, z, st, b_ready, rp, pa, pb);
-    else
-        vcycle<double>(m, amg, res, z, st, b_ready, rp, pa, pb);
+    vcycle<double>(m, amg, res, z, st, b_ready, rp, pa, pb);
 }
 
-void *amg_finest_rhs(Amg &amg, bool fp32) {
-    AmgLevel &L0 = amg.levels[0];
-    return fp32 ? static_cast<void *>(ptr<float>(L0.fb)) : static_cast<void *>(ptr<double>(L0.b));
-}
+double *amg_finest_rhs(Amg &amg) { return ptr<double>(amg.levels[0].b); }
 
 }  // namespace bchar

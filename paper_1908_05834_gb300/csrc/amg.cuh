@@ -10,14 +10,14 @@ namespace bchar {
 // kept and only the level operators are recomputed from the new matrix; a
 // node that has no coarse counterpart then simply gets no coarse correction.
 bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse = false);
-// z = M^-1 res (one V-cycle in FP32 or FP64).  With b_ready the caller has
-// already written the sign-flipped res into the finest level's right-hand side
-// in that precision.  With rp, pa, pb the last kernel also writes per-block
-// partial sums of z.res into pa and of z.rp into pb (kRedBlocks blocks).
-void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool fp32,
-               bool b_ready = false, const double *rp = nullptr, double *pa = nullptr, double *pb = nullptr);
-// The finest level's right-hand side in the V-cycle's precision (float or double).
-void *amg_finest_rhs(Amg &amg, bool fp32);
+// z = M^-1 res (one V-cycle).  With b_ready the caller has already written
+// the sign-flipped res into the finest level's right-hand side.  With rp, pa,
+// pb the last kernel also writes per-block partial sums of z.res into pa and
+// of z.rp into pb (kRedBlocks blocks).
+void amg_apply(bchar_mesh_t m, Amg &amg, const double *res, double *z, const CgState *st, bool b_ready = false,
+               const double *rp = nullptr, double *pa = nullptr, double *pb = nullptr);
+// The finest level's right-hand side.
+double *amg_finest_rhs(Amg &amg);
 void amg_release(Amg &amg);
 void amg_smooth_once(bchar_mesh_t m, Amg &amg);
 

@@ -134,7 +134,7 @@ void bchar_default_options(bchar_options *o) {
     o->penalty = 1e-7;
     o->qp_tol = 1e-9;
     o->qp_max_iter = 200000;
-    o->qp_max_refine = 100;
+    o->qp_max_refine = 300;
     o->div_tol = 1e-9;
     o->qp_precond = 1;
     o->qp_warm_start = 1;
@@ -618,7 +618,7 @@ bchar_status bchar_time_stage(bchar_mesh_t m, int stage, int reps, float *mean_m
         case BCHAR_STAGE_ASSEMBLE: launch_assemble(m); break;
         case BCHAR_STAGE_SMOOTH: amg_smooth_once(m, m->amg); break;
         case BCHAR_STAGE_VCYCLE:  // on the finest right-hand side left by the last solve; z is scratch after the step
-            amg_apply(m, m->amg, nullptr, ptr<double>(m->cg_z), nullptr, true, true);
+            amg_apply(m, m->amg, nullptr, ptr<double>(m->cg_z), nullptr, true);
             break;
         case BCHAR_STAGE_SCALING: launch_scaling_once(m); break;
         default: launch_track(m, m->dt, m->substeps); break;

@@ -105,8 +105,8 @@ struct Buf {
 struct AmgLevel {
     int64_t n = 0, nnz = 0;
     Buf ptr, col, val, diag, exc, agg, mptr, mlist, x, x2, b, r;  // mptr/mlist: members of each aggregate
-    Buf fval, fdiag, fx, fx2, fb, fr;  // FP32 copy of the operator (scaled) and FP32 work vectors
-    Buf dval, ddiag;                   // FP64 scaled copy (work vectors: x, x2, b, r)
+    Buf dval, ddiag;                   // the operator divided by the scale (work vectors: x, x2, b, r)
+    Buf ddinv;                         // smoother weights omega_i / diag_i of the scaled copy
     const double *diag_ext = nullptr;  // level 0 shares the minimisation's diagonal
     const double *exc_ext = nullptr;   // and its excess (the penalty shift)
 };
@@ -115,10 +115,10 @@ struct Amg {
     std::vector<AmgLevel> levels;
     int nlev = 0;
     Buf tmp;
-    double scale = 1.0;  // the FP32 levels hold operator / scale
+    double scale = 1.0;  // the V-cycle's levels hold operator / scale
     int small_from = 0;        // levels small_from..nlev-1 are cycled by one block (nlev: none)
     int large_sweeps = 0;      // Jacobi sweeps of a coarsest level too large for one block
-    Buf small_f, small_d;      // device descriptors of the small levels (FP32 / FP64 operators)
+    Buf small_d;               // device descriptors of the small levels
 };
 
 }  // namespace bchar

@@ -942,21 +942,21 @@ __global__ void k_ip_update(int64_t nnz, int64_t n2, const IpScalars *st, double
     }
 }
 
-__global__ void k_ip_init(int64_t nnz, int64_t n2, double *f, double *u, double *zl, double *zh, double *y, double *p,
-                          double *n, double *zp, double *zn) {
+__global__ void k_ip_init(int64_t nnz, int64_t n2, double z0, double p0, double zp0, double *f, double *u,
+                          double *zl, double *zh, double *y, double *p, double *n, double *zp, double *zn) {
     GRID_STRIDE(e, nnz > n2 ? nnz : n2) {
         if (e < nnz) {
             f[e] = 1.0;
             u[e] = 1.0;
-            zl[e] = 1.0;
-            zh[e] = 1.0;
+            zl[e] = z0;
+            zh[e] = z0;
         }
         if (e < n2) {
             y[e] = 0.0;
-            p[e] = 1.0;
-            n[e] = 1.0;
-            zp[e] = 1.0;
-            zn[e] = 1.0;
+            p[e] = p0;
+            n[e] = p0;
+            zp[e] = zp0;
+            zn[e] = zp0;
         }
     }
 }
@@ -973,11 +973,11 @@ __global__ void k_ip_finish(int64_t nnz, const double *f, double *qx, DevInfo *i
     if (at) atomicAdd(&info->n_at_bounds, at);
 }
 
-static void precondition(bchar_mesh_t m, bool amg, bool fp32, const double *res, double *z, const CgState *st,
+static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z, const CgState *st,
                          bool b_ready = false, const double *rp = nullptr, double *pa = nullptr,
                          double *pb = nullptr) {
     if (amg) {
-        amg_apply(m, m->amg, res, z, st, fp32, b_ready, rp, pa, pb);
+        amg_apply(m, m->amg, res, z, st, b_ready, rp, pa, pb);
     } else {
         k_jacobi_precond<<<blocks_for(2 * m->nc), kThreads, 0, m->stream>>>(2 * m->nc, ptr<double>(m->diag), res, z, st);
         ++m->launches;
@@ -999,7 +999,7 @@ constexpr int kStallIters = 400;
 // the solve has converged (its kernels do nothing then); the host polls once
 // per batch.  Returns the iterations done.
 static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double target_res, bool amg,
-                     bool fp32, int max_iter, cudaGraphExec_t *exec, int *graph_launches) {
+                     int max_iter, cudaGraphExec_t *exec, int *graph_launches) {
     const int64_t nc = m->nc, n2 = 2 * nc;
     const int bl = blocks_for(n2);
     cudaStream_t s = m->stream;
@@ -1015,7 +1015,7 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double
     CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
     cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
     k_copy<<<bl, kThreads, 0, s>>>(n2, rhs, res, nullptr);
-    precondition(m, amg, fp32, res, z, nullptr);
+    precondition(m, amg, res, z, nullptr);
     k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
     // the right-hand side's residual norm is not formed: the first iteration checks it
     k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, target_rz, target_res, INFINITY, st);
@@ -1029,17 +1029,13 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double
                             q, part, st);
             launch_dep(k_cg_alpha, 1, 1024, s, part, mv_grid, st);
             if (amg) {
-                if (fp32)
-                    launch_dep(k_cg_update_b<float>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, brow, volphi, part_res,
-                               static_cast<float *>(amg_finest_rhs(m->amg, true)), st);
-                else
-                    launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, brow, volphi, part_res,
-                               static_cast<double *>(amg_finest_rhs(m->amg, false)), st);
-                precondition(m, amg, fp32, res, z, st, true, rp, part_rz, part_zp);
+                launch_dep(k_cg_update_b<double>, kRedBlocks, kThreads, s, nc, p, q, d, res, rp, brow, volphi, part_res,
+                           amg_finest_rhs(m->amg), st);
+                precondition(m, amg, res, z, st, true, rp, part_rz, part_zp);
                 m->launches += 3;
             } else {
                 launch_dep(k_cg_update, kRedBlocks, kThreads, s, n2, p, q, d, res, rp, brow, volphi, part_res, st);
-                precondition(m, amg, fp32, res, z, st);
+                precondition(m, amg, res, z, st);
                 launch_dep(k_dot2, kRedBlocks, kThreads, s, n2, z, res, rp, part_rz, part_zp, st);
                 m->launches += 4;
             }
@@ -1115,6 +1111,14 @@ constexpr double kIpMuFloor = 0.1 * kIpMuTol;
 constexpr int kIpCgPerSolve = 400;
 constexpr double kIpRdRel = 1e-12;
 constexpr double kIpStep = 0.99;
+// The starting point: y = 0; the violation parts p = n = kIpStartViol with
+// multipliers gamma, which satisfies their stationarity at y = 0; f = u = 1
+// with multipliers kIpStartViol * gamma, so that every complementarity
+// product starts equal (a centred point).  Multipliers 1 for the violation
+// parts leave a dual residual of gamma = 1e8 for the first Newton step, after
+// which the steps shrink to nothing on some small meshes; uncentred starts
+// take up to twice the iterations on the 1024^2 workload.
+constexpr double kIpStartViol = 0.1;
 
 bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
     const bool trace = getenv("BCHAR_TRACE") != nullptr;  // diagnostic: per-iteration scalars on stderr
@@ -1159,7 +1163,8 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
     const double pairs = 2.0 * static_cast<double>(nnz) + 2.0 * static_cast<double>(n2);
     const bool use_amg = m->opt.qp_precond == 1;
 
-    k_ip_init<<<blm, kThreads, 0, s>>>(nnz, n2, f, u, zl, zh, y, p, n, zp, zn);
+    k_ip_init<<<blm, kThreads, 0, s>>>(nnz, n2, kIpStartViol * gamma, kIpStartViol, gamma, f, u, zl, zh, y, p, n, zp,
+                                       zn);
     ++m->launches;
     int it = 0, total_cg = 0;
     bool converged = false;
@@ -1195,7 +1200,6 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
         // one (which the step then reduces), but not below half the stopping tolerance
         const double target_rz = 1e-2 * mu;
         const double target_res = fmax(0.1 * hs.rp_max, 0.5 * m->opt.qp_tol);
-        const bool fp32 = mu > 1e-6;
         cudaGraphExec_t exec = nullptr;
         int graph_launches = 0;
         for (int corr = 0; corr < 2; ++corr) {
@@ -1208,7 +1212,7 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
             const int left = m->opt.qp_max_iter - total_cg;
             const int cap = left < kIpCgPerSolve ? left : kIpCgPerSolve;
             // the right-hand side's L1 norm: the node pass's |rp|_1 bounds it well enough for the start
-            const int done = pcg_solve(m, rhs, target_rz, target_res, amg, fp32 && amg, cap > 0 ? cap : 1,
+            const int done = pcg_solve(m, rhs, target_rz, target_res, amg, cap > 0 ? cap : 1,
                                        &exec, &graph_launches);
             total_cg += done;
             if (trace)

@@ -19,6 +19,8 @@ Tolerances (from the arithmetic):
     maximum is reported.
   * Mass: |M^{n+1} - M^n| <= 1e-12 M^n on the GPU in both modes.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -264,7 +266,7 @@ def test_fp32_split_error_budget(bc, name):
     mesh.close()
 
 
-FULL_SIZE_IP_ITERS = 25  # the cap the benchmark steps run with
+FULL_SIZE_IP_ITERS = 25  # interior-point iterations of the 256^3 step
 
 
 @pytest.mark.parametrize("name,precision", [("vortex2d_1024", 1), ("deform3d_128", 1), ("deform3d_256", 1)])
@@ -274,21 +276,19 @@ def test_full_size_sampled_rows(bc, name, precision):
     256^3 workload keeps c in FP32 (its stored mass is checked too); its
     matrix is read row by row from the exported arrays (no sparse copy).
 
-    The minimisation runs under the benchmarked cap of interior-point
-    iterations: at these sizes a converged solve takes tens of seconds
-    (the step reports qp_converged = 0 then), while every other invariant
-    (bounds, exact column masses, exact global mass) holds at any iterate."""
-    if name == "deform3d_256":
-        # one step holds about 264 GB while a row wider than the slab makes the
-        # slab that wide for every row (measured on a 284 GB device)
-        import torch
-        free, _ = torch.cuda.mem_get_info()
-        if free < 270e9:
-            pytest.skip(f"needs about 270 GB of free device memory, {free / 1e9:.0f} GB free")
+    The minimisation is solved to the default tolerance (as benchmarked)
+    on the 1024^2 and 128^3 workloads.  On 256^3 a converged solve takes
+    minutes, so there it stops after FULL_SIZE_IP_ITERS iterations and
+    qp_converged is not asserted; every other invariant (bounds, exact column
+    masses, exact global mass) holds at any iterate."""
+    if name == "deform3d_256" and os.environ.get("BCHAR_FULL_256") != "1":
+        # its 25 capped interior-point iterations alone ran past 15 minutes on one GB300
+        pytest.skip("one 256^3 step takes more than 15 minutes (minimisation); set BCHAR_FULL_256=1 to run it")
     wl = inputs.workload(name)
     faces = wl.faces(0)
     c = wl.c0 if wl.c_dtype == "f32" else wl.c0.astype(np.float64)
-    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c, precision=precision, qp_max_refine=FULL_SIZE_IP_ITERS)
+    cap = {"qp_max_refine": FULL_SIZE_IP_ITERS} if name == "deform3d_256" else {}
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c, precision=precision, **cap)
     om = oracle.Mesh(wl.coords, wl.phi)
     rng = np.random.Generator(np.random.PCG64(99))
     rows = np.sort(rng.choice(om.nc, size=48, replace=False))
@@ -331,7 +331,8 @@ def test_full_size_sampled_rows(bc, name, precision):
           f"{info['kkt_rel']:.1e}, entries at bounds {info['n_at_bounds']}, max row residual "
           f"{info['max_rel_row_res']:.2e}, minimisation {info['ms_stage']['minimise']:.0f} ms, "
           f"converged {info['qp_converged']}")
-    assert info["ip_iters"] <= FULL_SIZE_IP_ITERS
+    if name != "deform3d_256":
+        assert info["qp_converged"]
     assert info["n_at_bounds"] >= 0 and info["spill_rows"] >= 0
     assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
     assert info["max_rel_col_res"] <= 1e-13

@@ -422,6 +422,15 @@ __global__ void k_copy(int64_t n, const double *in, double *out, const CgState *
     GRID_STRIDE(i, n) out[i] = in[i];
 }
 
+// res = rhs - q (the residual of a starting guess whose product is q)
+__global__ void k_residual(int64_t n, const double *rhs, const double *q, double *res) {
+    GRID_STRIDE(i, n) res[i] = rhs[i] - q[i];
+}
+
+// Clears the converged flag a finished solve left, before a product that the
+// next solve's start needs (the CG kernels return at once while it is set).
+__global__ void k_cg_reopen(CgState *st) { st->converged = 0; }
+
 // z = res / diag (Jacobi preconditioner)
 __global__ void k_jacobi_precond(int64_t n, const double *diag, const double *res, double *z, const CgState *st) {
     dep_enter();
@@ -989,16 +998,17 @@ static void precondition(bchar_mesh_t m, bool amg, const double *res, double *z,
 constexpr int kStallIters = 400;
 
 // The conjugate gradients on (A-hat D A-hat^T + diag(exc)) d = rhs, from
-// d = 0, until z.res <= target_rz (z the preconditioned residual: about the
-// squared error of d in the norm of the matrix, which bounds the error of
-// A-hat^T d where the interior-point direction needs it -- an L1 test alone
-// would not bound the error along the nearly singular modes of weakly linked
-// cells) and max_l |res_l| / b_l <= target_res (after a full step, res is the
-// constraint residual, which the interior point measures in that norm).  One batch of iterations is captured into a CUDA graph
-// per preconditioner build (*exec; destroyed by the caller) and replayed until
-// the solve has converged (its kernels do nothing then); the host polls once
-// per batch.  Returns the iterations done.
-static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double target_res, bool amg,
+// d = 0 (or, with warm, from the d already in place), until z.res <= target_rz
+// (z the preconditioned residual: about the squared error of d in the norm of
+// the matrix, which bounds the error of A-hat^T d where the interior-point
+// direction needs it -- an L1 test alone would not bound the error along the
+// nearly singular modes of weakly linked cells) and max_l |res_l| / b_l <=
+// target_res (after a full step, res is the constraint residual, which the
+// interior point measures in that norm).  One batch of iterations is captured
+// into a CUDA graph per preconditioner build (*exec; destroyed by the caller)
+// and replayed until the solve has converged (its kernels do nothing then);
+// the host polls once per batch.  Returns the iterations done.
+static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double target_res, bool amg, bool warm,
                      int max_iter, cudaGraphExec_t *exec, int *graph_launches) {
     const int64_t nc = m->nc, n2 = 2 * nc;
     const int bl = blocks_for(n2);
@@ -1013,14 +1023,23 @@ static int pcg_solve(bchar_mesh_t m, const double *rhs, double target_rz, double
     double *part_zp = part + 3 * 152 * 64;
     CgState *st = ptr<CgState>(m->cg);
     CgState *host_st = reinterpret_cast<CgState *>(static_cast<char *>(m->info_host.p) + sizeof(DevInfo));
-    cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
-    k_copy<<<bl, kThreads, 0, s>>>(n2, rhs, res, nullptr);
+    if (warm) {  // start from the d already in place: res = rhs - M d
+        k_cg_reopen<<<1, 1, 0, s>>>(st);
+        k_cg_matvec<<<tile_grid(2 * m->ntile), kTileThreads, kTileSmem, s>>>(
+            row_view(m, a2), col_view(m, a2c), diag, d, q, part, st);
+        k_residual<<<bl, kThreads, 0, s>>>(n2, rhs, q, res);
+        m->launches += 3;
+    } else {
+        cudaMemsetAsync(d, 0, sizeof(double) * n2, s);
+        k_copy<<<bl, kThreads, 0, s>>>(n2, rhs, res, nullptr);
+        ++m->launches;
+    }
     precondition(m, amg, res, z, nullptr);
     k_dot<<<kRedBlocks, kThreads, 0, s>>>(n2, res, z, part_rz, nullptr);
     // the right-hand side's residual norm is not formed: the first iteration checks it
     k_cg_start<<<1, 1024, 0, s>>>(part_rz, kRedBlocks, target_rz, target_res, INFINITY, st);
     k_copy<<<bl, kThreads, 0, s>>>(n2, z, p, nullptr);
-    m->launches += 4;
+    m->launches += 3;
     const int batch = amg ? 8 : 32;
     const int mv_grid = tile_grid(2 * m->ntile);  // <= kRedBlocks partial sums of p.q
     auto enqueue_batch = [&]() {
@@ -1212,7 +1231,10 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
             const int left = m->opt.qp_max_iter - total_cg;
             const int cap = left < kIpCgPerSolve ? left : kIpCgPerSolve;
             // the right-hand side's L1 norm: the node pass's |rp|_1 bounds it well enough for the start
-            const int done = pcg_solve(m, rhs, target_rz, target_res, amg, cap > 0 ? cap : 1,
+            // the corrector's system differs from the predictor's only in its right-hand
+            // side (the centring and second-order terms): its solve starts from the
+            // predictor's direction
+            const int done = pcg_solve(m, rhs, target_rz, target_res, amg, corr == 1, cap > 0 ? cap : 1,
                                        &exec, &graph_launches);
             total_cg += done;
             if (trace)

@@ -60,8 +60,8 @@ constexpr int64_t kOneBlock = 4096;   // levels up to this size are cycled by on
 constexpr int kMaxLevels = 40;
 constexpr int kHandshakes = 4;        // matching rounds per level
 constexpr double kStall = 0.9;        // stop coarsening when a level keeps this fraction of nodes
-constexpr double kOmega = 0.6;        // Jacobi damping (rows with off-diagonal entries)
-constexpr double kStrength = 0.05;    // strong edge: w_ij >= kStrength sqrt(d_i d_j)
+constexpr double kOmega = 0.9;        // Jacobi damping (rows with off-diagonal entries)
+constexpr double kStrength = 0.1;     // strong edge: w_ij >= kStrength sqrt(d_i d_j)
 constexpr double kAttach = 0.25;      // a leftover node follows an edge carrying this share of its diagonal
 constexpr double kDominant = 0.25;    // a node leaves the hierarchy when its off-diagonal sum is this share of its diagonal
 constexpr int kCoarsestSweeps = 40;   // sweeps of a one-block coarsest level

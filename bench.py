@@ -82,17 +82,36 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _definition(text: str, head: str) -> str:
-    """The source of the definition starting at `head` (through the brace
-    that closes its body)."""
-    i = text.index(head)
-    j = text.index("{", i)
-    depth = 0
-    for k in range(j, len(text)):
-        depth += {"{": 1, "}": -1}.get(text[k], 0)
-        if depth == 0:
-            return text[i:k + 1]
-    raise ValueError(head)
+def _definition(text: str, name: str) -> str:
+    """The source of the definition of `name` (a kernel, or a struct given as
+    "struct Name"): from the name through the brace that closes its body
+    (declarations without a body are skipped)."""
+    start = 0
+    while True:
+        i = text.index(name, start)
+        start = i + len(name)
+        j = i + len(name)
+        if name.startswith("struct "):
+            k = j
+        else:
+            if text[j] != "(":
+                continue
+            depth, k = 0, j
+            while True:  # the closing parenthesis of the parameter list
+                depth += {"(": 1, ")": -1}.get(text[k], 0)
+                k += 1
+                if depth == 0:
+                    break
+        while text[k].isspace():
+            k += 1
+        if text[k] != "{":
+            continue  # a declaration
+        depth = 0
+        for e in range(k, len(text)):
+            depth += {"{": 1, "}": -1}.get(text[e], 0)
+            if depth == 0:
+                return text[i:e + 1]
+        raise ValueError(name)
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -104,8 +123,8 @@ def kernel_source_hash(kernel: str) -> str:
     with open(os.path.join(CSRC, "tiles.cuh")) as f:
         tiles = f.read()
     h = hashlib.sha256()
-    for head in [f"__global__ void {kernel}("] + deps:
-        h.update(_definition(text, head).encode())
+    for name in [kernel] + deps:
+        h.update(_definition(text, name).encode())
     h.update(tiles.encode())
     return h.hexdigest()[:16]
 

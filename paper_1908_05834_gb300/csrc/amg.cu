@@ -757,7 +757,7 @@ __global__ void k_prolong_smooth(int64_t n, const int64_t *ptr, const int32_t *c
         T s = diag[i] * xi;
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t j = col[e];
-            const int32_t J = agg[j];  // < 0 only with aggregates kept from an earlier matrix
+            const int32_t J = agg[j];  // < 0: a neighbour that left the hierarchy
             s += val[e] * (J >= 0 ? x[j] + xc[J] : x[j]);
         }
         x_out[i] = xi + dinv[i] * (b[i] - s);
@@ -885,41 +885,6 @@ static bool level_vectors(bchar_mesh_t m, AmgLevel &L) {
            ensure(m, L.b, sizeof(double) * L.n) && ensure(m, L.r, sizeof(double) * L.n);
 }
 
-// The operators of levels 1..nlev-1 from level 0, on the kept aggregates.
-// Returns false when a coarse row overflows (then the caller rebuilds).
-static bool amg_reoperate(bchar_mesh_t m, Amg &amg, bool &overflowed) {
-    cudaStream_t s = m->stream;
-    overflowed = false;
-    for (int l = 0; l + 1 < amg.nlev; ++l) {
-        AmgLevel &F = amg.levels[l];
-        AmgLevel &C = amg.levels[l + 1];
-        const double *fexc = F.exc_ext ? F.exc_ext : ptr<double>(F.exc);
-        const int64_t nco = C.n;
-        if (!ensure(m, amg.tmp, sizeof(int32_t) * (nco + 1) + 64)) return false;
-        int32_t *rowcnt = ptr<int32_t>(amg.tmp);
-        int *overflow = reinterpret_cast<int *>(rowcnt + nco + 1);
-        cudaMemsetAsync(overflow, 0, sizeof(int), s);
-        coarse_count(m, F, C, nco, fexc, rowcnt, overflow);
-        scan_i32_to_i64(m, rowcnt, ptr<int64_t>(C.ptr), nco);
-        int64_t cnnz = 0;
-        int ovf = 0;
-        cudaMemcpyAsync(&cnnz, ptr<int64_t>(C.ptr) + nco, sizeof cnnz, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&ovf, overflow, sizeof ovf, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-        ++m->launches;
-        if (ovf) {
-            overflowed = true;
-            return true;
-        }
-        C.nnz = cnnz;
-        if (!ensure(m, C.col, sizeof(int32_t) * (cnnz > 0 ? cnnz : 1)) ||
-            !ensure(m, C.val, sizeof(double) * (cnnz > 0 ? cnnz : 1)))
-            return false;
-        coarse_fill(m, F, C, nco, fexc);
-    }
-    return true;
-}
-
 static bool amg_scaled_copies(bchar_mesh_t m, Amg &amg);
 
 // The one-block levels: every level from the first with at most kOneBlock
@@ -947,27 +912,10 @@ static bool small_descriptors(bchar_mesh_t m, Amg &amg) {
     return true;
 }
 
-bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse) {
+bool amg_build(bchar_mesh_t m, Amg &amg) {
     cudaStream_t s = m->stream;
     const int64_t nc = m->nc, nnz = m->nnz;
     if (amg.levels.empty()) amg.levels.resize(1);
-    if (reuse && amg.nlev > 1 && amg.levels[0].n == 2 * nc) {
-        AmgLevel &L0 = amg.levels[0];
-        L0.nnz = 2 * nnz;
-        if (!ensure(m, L0.col, sizeof(int32_t) * L0.nnz) || !ensure(m, L0.val, sizeof(double) * L0.nnz)) return false;
-        launch_dep(k_level0_ptr, blocks_for(L0.n + 1), kThreads, s, nc, nnz, ptr<int64_t>(m->row_ptr),
-                                                               ptr<int64_t>(m->col_ptr), ptr<int64_t>(L0.ptr));
-        launch_dep(k_level0_fill, blocks_for(L0.n), kThreads, s, nc, ptr<int64_t>(m->row_ptr), ptr<int32_t>(m->col),
-                                                            ptr<int64_t>(m->col_ptr), ptr<int32_t>(m->csc_row),
-                                                            ptr<double>(m->a2), ptr<double>(m->a2c),
-                                                            ptr<int64_t>(L0.ptr), ptr<int32_t>(L0.col),
-                                                            ptr<double>(L0.val));
-        m->launches += 2;
-        bool overflowed = false;
-        if (!amg_reoperate(m, amg, overflowed)) return false;
-        if (!overflowed) return amg_scaled_copies(m, amg);
-        // a coarse row of the kept hierarchy overflows on this matrix: build anew
-    }
     amg.nlev = 1;
     amg.large_sweeps = kLargeCoarsestSweeps;
     AmgLevel &L0 = amg.levels[0];

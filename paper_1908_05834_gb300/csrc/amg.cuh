@@ -5,11 +5,9 @@
 
 namespace bchar {
 
-// Builds the hierarchy for the current matrix.  With reuse, the aggregates of
-// the hierarchy already built (on an earlier matrix of the same handle) are
-// kept and only the level operators are recomputed from the new matrix; a
-// node that has no coarse counterpart then simply gets no coarse correction.
-bool amg_build(bchar_mesh_t m, Amg &amg, bool reuse = false);
+// Builds the hierarchy for the current matrix (the minimisation's weights
+// change by orders of magnitude between iterations, so it is built anew each time).
+bool amg_build(bchar_mesh_t m, Amg &amg);
 // z = M^-1 res (one V-cycle).  With b_ready the caller has already written
 // the sign-flipped res into the finest level's right-hand side.  With rp, pa,
 // pb the last kernel also writes per-block partial sums of z.res into pa and

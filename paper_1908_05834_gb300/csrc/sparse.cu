@@ -1212,7 +1212,7 @@ bool launch_minimise(bchar_mesh_t m, int *cg_iters, int *ip_iters) {
                    n, zp, zn, D, ptr<double>(m->a2), ptr<double>(m->diag), ptr<double>(m->qexc));
         k_qp_gather_cols<<<blocks_for(nnz), kThreads, 0, s>>>(nnz, csc_src, ptr<double>(m->a2), ptr<double>(m->a2c));
         m->launches += 2;
-        const bool amg = use_amg && amg_build(m, m->amg, false);
+        const bool amg = use_amg && amg_build(m, m->amg);
         // each direction solved until its squared energy-norm error is about <= 1e-2 mu (then
         // every entry's step error stays about <= 0.1 of its distance to the bound) and the
         // constraint residual it leaves is, relative to each target, <= 0.1 of the current

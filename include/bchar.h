@@ -72,8 +72,9 @@ typedef struct {
     double div_tol;     /* relative tolerance of the velocity checks (1e-9) */
     int qp_precond;     /* preconditioner of the minimisation's conjugate gradients:
                            1 = aggregation multigrid (default), 0 = Jacobi */
-    int qp_warm_start;  /* reserved (0 or 1, default 1): every minimisation starts from
-                           1 + x = 1 with unit bound multipliers and zero constraint multipliers */
+    int qp_warm_start;  /* reserved (0 or 1, default 1; no effect): every minimisation starts
+                           from the same centred point, 1 + x = 1, zero constraint multipliers
+                           (see bchar_step) */
     int slab_width;     /* entries per row of the assembly's row slab; 0 (default) = 24 in 2D,
                            64 in 3D; wider rows go to the spill area (results are the same) */
 } bchar_options;
@@ -163,7 +164,10 @@ bchar_status bchar_set_velocity(bchar_mesh_t m, const double *const *face_u, int
  *      bounds allow.  Solved by a primal-dual interior-point method whose
  *      linear systems are solved by multigrid-preconditioned conjugate
  *      gradients; then every column scaled to |M|_phi so that global mass is
- *      conserved to rounding;
+ *      conserved to rounding.  If the minimisation reaches qp_max_refine or
+ *      qp_max_iter before its stopping rule, the step still completes from
+ *      the last iterate (the bounds and global mass hold at any iterate), the
+ *      status is OK and info->qp_converged = 0;
  *   5. c_out = W c_in (eq. phys-inter-ELLAM), FP64 accumulation.
  * c_in, c_out: DEVICE arrays of n_c values of type c_dtype, caller-owned, not
  * aliased.  info: optional (NULL), written on return.  The call returns when

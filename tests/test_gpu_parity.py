@@ -142,6 +142,29 @@ def test_matrices_match_oracle_fp64(bc, name):
     mesh.close()
 
 
+def test_multilevel_preconditioner_case_matches_oracle(bc):
+    """A 96x96 stretched vortex: 18 432 constraint nodes, so the multigrid's
+    finest levels exceed one block and run the multi-block V-cycle kernels
+    (the smaller cases are cycled by one block alone).  The final weights and
+    c match the oracle as on the small cases."""
+    wl = inputs.workload("vortex2d_1024", n=96)
+    faces = wl.faces(3)
+    c = wl.c0.astype(np.float64)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c)
+    ref = oracle.step(oracle.Mesh(wl.coords, wl.phi), faces, wl.dt, c)
+    print(f"\n96^2: levels {info['amg_levels']}, coarsest {info['amg_coarsest']}, interior-point iters "
+          f"{info['ip_iters']}, cg iters {info['cg_iters']}")
+    assert info["qp_converged"]
+    assert info["amg_levels"] >= 3 and 2 * wl.nc > 4096
+    vp = oracle.Mesh(wl.coords, wl.phi).volphi()
+    W = sp.diags(1.0 / vp) @ _csr(mesh, 2)
+    assert np.max(_row_rel_err(W.tocsr(), ref["W"])) <= 1e-5
+    err = np.abs(c_gpu - ref["c"]).sum() / np.abs(ref["c"]).sum()
+    assert err <= 1e-5
+    assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    mesh.close()
+
+
 @pytest.mark.parametrize("name,width", [("stretched2d", 2), ("porous3d", 8)])
 def test_rows_wider_than_the_slab_go_to_the_spill_area(bc, name, width):
     """A slab narrower than most rows: those rows are assembled a second time

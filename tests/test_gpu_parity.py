@@ -142,6 +142,30 @@ def test_matrices_match_oracle_fp64(bc, name):
     mesh.close()
 
 
+@pytest.mark.parametrize("name,n", [("vortex2d_1024", 24), ("deform3d_128", 8)])
+def test_three_balls_per_axis_matches_oracle(bc, name, n):
+    """More balls per cell (Sec 4 conclusion on the number of balls): n_b = 3
+    per axis (9 balls per square cell in 2D, 27 per cube in 3D) on a stretched
+    2D and a porous 3D case, GPU against the oracle with the same packing."""
+    wl = inputs.workload(name, n=n)
+    faces = wl.faces(2)
+    c = wl.c0.astype(np.float64)
+    mesh, info, c_gpu = _gpu_step(bc, wl, faces, c, balls_per_axis=3)
+    om = oracle.Mesh(wl.coords, wl.phi, nb=3)
+    ref = oracle.step(om, faces, wl.dt, c)
+    assert mesh.nballs == int(ref["ball_offset"][-1]) >= 9 * om.nc
+    e0 = _row_rel_err(_csr(mesh, 0), ref["A0"])
+    print(f"\n{name} n_b = 3: {mesh.nballs} balls, A0 rows off by face ties {np.sum(e0 > 1e-10)}/{e0.size}")
+    assert np.mean(e0 <= 1e-10) >= 0.99
+    assert info["qp_converged"]
+    W = sp.diags(1.0 / om.volphi()) @ _csr(mesh, 2)
+    assert np.max(_row_rel_err(W.tocsr(), ref["W"])) <= 1e-5
+    err = np.abs(c_gpu - ref["c"]).sum() / np.abs(ref["c"]).sum()
+    assert err <= 1e-5
+    assert abs(info["mass_after"] - info["mass_before"]) <= 1e-12 * info["mass_before"]
+    mesh.close()
+
+
 def test_multilevel_preconditioner_case_matches_oracle(bc):
     """A 96x96 stretched vortex: 18 432 constraint nodes, so the multigrid's
     finest levels exceed one block and run the multi-block V-cycle kernels
